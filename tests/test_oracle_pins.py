@@ -1,0 +1,291 @@
+"""Pins for the CPU oracle (CPU only).
+
+The oracle is checked against things other than itself: the paper's printed
+outcomes (Table "table:concur", the claims around Figure "fig:dfalong"),
+closed forms, independent algorithms (Hopcroft's n log n method, the pair-graph
+characterisation of Section 3.1, word enumeration, Hopcroft-Karp with
+union-find, breadth-first product search), and invariants.  The last tests
+plant mistakes in the oracle and check that the pins catch them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import dfagen
+import oracle
+from conftest import GOLDEN
+
+
+def _table_rows():
+    rows = {}
+    with open(os.path.join(GOLDEN, "table_concur.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            rows[p[0]] = dict(N=int(p[1]), k=int(p[2]), size=int(p[3]), naive=p[4], sort=p[5], trans=p[6])
+    return rows
+
+
+def _tiny_random(seed, n, k, p=0.5):
+    return dfagen.random_dfa(n, k, p, seed)
+
+
+# ---------------------------------------------------------------- whole partition
+
+@pytest.mark.parametrize("n,k,p,seed", [(50, 1, 0.5, 1), (200, 2, 0.5, 2), (1000, 3, 0.3, 3),
+                                        (5000, 4, 0.5, 4), (3000, 8, 0.1, 5), (777, 2, 0.9, 6)])
+def test_moore_equals_hopcroft_random(n, k, p, seed):
+    A = dfagen.random_dfa(n, k, p, seed)
+    assert np.array_equal(oracle.moore(A.delta, A.accept).block, oracle.hopcroft(A.delta, A.accept))
+
+
+def test_moore_equals_brute_force_tiny():
+    """n <= 7, k <= 3: Moore = pair-table backward search = word enumeration."""
+    checked = 0
+    for seed in range(120):
+        n = 1 + seed % 7
+        k = 1 + (seed // 7) % 3
+        A = _tiny_random(seed, n, k, p=[0.5, 0.3, 0.7][seed % 3])
+        m = oracle.moore(A.delta, A.accept).block
+        assert np.array_equal(m, oracle.pair_table(A.delta, A.accept))
+        assert np.array_equal(m, oracle.word_enumeration(A.delta, A.accept))
+        checked += 1
+    assert checked == 120
+
+
+def test_tiny_dfas_with_merges_brute_force():
+    """Small DFAs with few targets have many equivalent states; all three agree."""
+    for seed in range(60):
+        n, k = 6 + seed % 3, 1 + seed % 2
+        d = dfagen.bounded(seed, 77, n * k, 3).reshape(k, n)    # targets only among states 0..2
+        acc = dfagen.bernoulli(seed, 78, n, 0.5)
+        m = oracle.moore(d, acc).block
+        assert np.array_equal(m, oracle.pair_table(d, acc))
+        assert np.array_equal(m, oracle.word_enumeration(d, acc))
+        assert np.array_equal(m, oracle.hopcroft(d, acc))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_planted_redundancy_closed_form(seed):
+    """Blowing every state of a minimal DFA up into copies: the coarsest partition
+    is exactly 'copies of the same state'."""
+    base = dfagen.random_dfa(400, 2 + seed, 0.5, seed + 10)
+    assert oracle.hopcroft(base.delta, base.accept).max() + 1 == base.n      # base is minimal
+    P, origin = dfagen.planted_redundancy(base, 5, seed)
+    expect = oracle.canonical(origin)
+    m = oracle.moore(P.delta, P.accept)
+    assert m.num_blocks == base.n
+    assert np.array_equal(m.block, expect)
+    assert np.array_equal(oracle.hopcroft(P.delta, P.accept), expect)
+    assert np.array_equal(oracle.naive_pr(P.delta, P.accept).block, expect)
+    assert np.array_equal(oracle.trans_pr(P.delta, P.accept).block, expect)
+
+
+# ---------------------------------------------------------------- paper's outcomes
+
+def test_table_concur_fib18_row():
+    """Fib_18 row: N = 6,765, output size N, naivePR and sortPR iterations N-1."""
+    row = _table_rows()["Fib_18"]
+    A = dfagen.fibonacci_dfa_with_states(row["N"])
+    m = oracle.moore(A.delta, A.accept)
+    assert m.num_blocks == row["size"]
+    assert m.rounds_executed == int(row["sort"])
+    assert m.rounds_changed == row["N"] - 2          # shortest distinguishing word has length n-2 (Section 3.3)
+    nv = oracle.naive_pr(A.delta, A.accept)
+    assert nv.num_blocks == row["size"] and nv.rounds_executed == int(row["naive"])
+
+
+@pytest.mark.parametrize("name", ["B_15", "B_16", "B_17"])
+def test_table_concur_bit_splitter_rows(name):
+    """B_m rows: output size 2^m; the printed iteration count m-1 is the number of
+    rounds that grow the partition; every round doubles the block count."""
+    row = _table_rows()[name]
+    m_ = int(name.split("_")[1])
+    B = dfagen.bit_splitter(m_)
+    assert B.n == row["N"] and B.k == row["k"]
+    r = oracle.moore(B.delta, B.accept)
+    assert r.num_blocks == row["size"]
+    assert r.rounds_changed == int(row["sort"])
+    assert r.counts[:-1] == [2 ** (i + 1) for i in range(m_)]
+    nv = oracle.naive_pr(B.delta, B.accept)
+    assert nv.rounds_changed == int(row["naive"]) and nv.num_blocks == row["size"]
+
+
+@pytest.mark.parametrize("i", range(3, 14))
+def test_fibonacci_rounds(i):
+    A = dfagen.fibonacci_dfa(i)
+    m = oracle.moore(A.delta, A.accept)
+    assert m.num_blocks == A.n and m.rounds_changed == A.n - 2 and m.rounds_executed == A.n - 1
+
+
+def test_fig1_claims():
+    """Section 3.4: without the closure, q0 and q1 need at least eight iterations;
+    with it, the first iteration already separates them."""
+    C = dfagen.fig1_chain()
+    m = oracle.moore(C.delta, C.accept, history=True)
+    sep = [h[0] != h[1] for h in m.history]
+    assert sep.index(True) == 8
+    assert m.rounds_changed == 8 and m.num_blocks == 10
+    nv = oracle.naive_pr(C.delta, C.accept, history=True)
+    assert [h[0] != h[1] for h in nv.history].index(True) == 8
+    t = oracle.naive_pr(oracle.closure(C.delta), C.accept, history=True)
+    assert t.history[1][0] != t.history[1][1]
+    assert t.num_blocks == 10
+
+
+@pytest.mark.parametrize("lg", [3, 5, 8, 10])
+def test_chain_closed_forms(lg):
+    n = 1 << lg
+    C = dfagen.chain_dfa(n)
+    T = oracle.closure(C.delta)
+    L = lg
+    i = np.arange(n)
+    for j in range(L + 1):
+        assert np.array_equal(T[0 * (L + 1) + j], np.minimum(i + (1 << j), n - 1))
+        assert (T[1 * (L + 1) + j] == 0).all()
+    m = oracle.moore(C.delta, C.accept)
+    assert m.num_blocks == n and m.rounds_changed == n - 2
+
+
+@pytest.mark.parametrize("n,k,seed", [(1, 2, 1), (2, 1, 2), (37, 3, 3), (300, 2, 4), (1025, 1, 5)])
+def test_closure_equals_repeated_application(n, k, seed):
+    A = dfagen.random_dfa(n, k, 0.5, seed)
+    T = oracle.closure(A.delta)
+    L = oracle.closure_levels(n)
+    assert T.shape == (k * (L + 1), n)
+    for a in range(k):
+        for lvl in range(L + 1):
+            cur = np.arange(n)
+            for _ in range(1 << lvl):
+                cur = A.delta[a][cur]
+            assert np.array_equal(T[a * (L + 1) + lvl], cur)
+
+
+# ---------------------------------------------------------------- naivePR / transPR
+
+@pytest.mark.parametrize("n,k,seed", [(300, 2, 1), (1000, 3, 2), (2000, 1, 3)])
+def test_naive_and_trans_equal_hopcroft(n, k, seed):
+    A = dfagen.random_dfa(n, k, 0.5, seed)
+    h = oracle.hopcroft(A.delta, A.accept)
+    assert np.array_equal(oracle.naive_pr(A.delta, A.accept).block, h)
+    assert np.array_equal(oracle.trans_pr(A.delta, A.accept).block, h)
+
+
+def test_naive_invariants():
+    """Leaders are the smallest member of their block; a round splits a block into
+    at most two parts; block counts never decrease."""
+    A = dfagen.random_dfa(500, 2, 0.5, 9)
+    r = oracle.naive_pr(A.delta, A.accept, history=True)
+    for prev, cur in zip(r.history, r.history[1:]):
+        assert oracle.is_refinement(cur, prev)
+        for b in np.unique(prev):
+            assert np.unique(cur[prev == b]).shape[0] <= 2
+    for h in r.history:
+        for b in np.unique(h):
+            assert b == np.nonzero(h == b)[0].min()
+    assert all(x <= y for x, y in zip(r.counts, r.counts[1:]))
+
+
+# ---------------------------------------------------------------- invariants, edges
+
+def test_moore_invariants():
+    A = dfagen.random_dfa(3000, 3, 0.5, 12)
+    r = oracle.moore(A.delta, A.accept, history=True)
+    for prev, cur in zip(r.history, r.history[1:]):
+        assert oracle.is_refinement(cur, prev)
+    assert all(x <= y for x, y in zip(r.counts, r.counts[1:]))
+    assert oracle.is_congruence(A.delta, r.block) and oracle.respects(A.accept, r.block)
+    assert oracle.is_canonical(r.block)
+
+
+def test_edge_cases():
+    # n = 1
+    r = oracle.moore(np.zeros((2, 1), np.uint32), np.array([1], np.uint8))
+    assert (r.num_blocks, r.rounds_changed, r.rounds_executed) == (1, 0, 1)
+    # k = 0: the result is {F, Q\F}
+    acc = np.array([0, 1, 1, 0, 1], np.uint8)
+    r = oracle.moore(np.zeros((0, 5), np.uint32), acc)
+    assert (r.num_blocks, r.rounds_changed, r.rounds_executed) == (2, 0, 1)
+    assert list(r.block) == [0, 1, 1, 0, 1]
+    # F empty / F = Q: one block
+    A = dfagen.random_dfa(100, 2, 0.0, 3)
+    assert oracle.moore(A.delta, A.accept).num_blocks == 1
+    A = dfagen.random_dfa(100, 2, 1.0, 3)
+    assert oracle.moore(A.delta, A.accept).num_blocks == 1
+    assert oracle.naive_pr(A.delta, A.accept).num_blocks == 1
+    with pytest.raises(ValueError):
+        oracle.moore(np.array([[5]], np.uint32), np.array([0], np.uint8))
+
+
+# ---------------------------------------------------------------- equivalence
+
+@pytest.mark.parametrize("req", range(10))
+def test_equivalence_recipe(req):
+    A, B, expect = dfagen.equivalence_pair(req, 5, n_lo=100, n_hi=3000)
+    e = oracle.equivalent(A.delta, A.accept, A.start, B.delta, B.accept, B.start)
+    assert e.equivalent == expect                                 # by construction
+    assert oracle.hk_equivalent(A.delta, A.accept, A.start, B.delta, B.accept, B.start) == expect
+    cex = oracle.shortest_cex(A.delta, A.accept, A.start, B.delta, B.accept, B.start)
+    assert (cex == -1) == expect
+    assert e.separated_round == cex                                # Moore round r = words of length <= r
+    ee = oracle.equivalent(A.delta, A.accept, A.start, B.delta, B.accept, B.start, early_exit=True)
+    assert ee.equivalent == expect and ee.separated_round == cex
+    if not expect:
+        assert ee.refine.rounds_executed == cex
+
+
+def test_equivalence_self_and_cycle():
+    C = dfagen.cycle_dfa(8)
+    assert oracle.equivalent(C.delta, C.accept, 0, C.delta, C.accept, 0).equivalent
+    # different start states of a minimal DFA are inequivalent
+    assert not oracle.equivalent(C.delta, C.accept, 0, C.delta, C.accept, 1).equivalent
+    assert not oracle.hk_equivalent(C.delta, C.accept, 0, C.delta, C.accept, 1)
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+def test_pins_catch_dropped_letter(monkeypatch):
+    """A signature that forgets the last letter must fail the Hopcroft pin."""
+    def bad_round(delta, block):
+        cols = [block] + [block[delta[a]] for a in range(delta.shape[0] - 1)]
+        return oracle.kernel_of(cols)
+    A = dfagen.random_dfa(400, 3, 0.5, 2)
+    good = oracle.moore(A.delta, A.accept).block
+    monkeypatch.setattr(oracle, "moore_round", bad_round)
+    assert not np.array_equal(oracle.moore(A.delta, A.accept).block, good)
+
+
+def test_pins_catch_missing_own_block(monkeypatch):
+    """Dropping block[q] from the signature breaks the refinement invariant on a
+    DFA where it matters (Fibonacci), caught by the table pin."""
+    def bad_round(delta, block):
+        return oracle.kernel_of([block[delta[a]] for a in range(delta.shape[0])])
+    A = dfagen.fibonacci_dfa(7)
+    monkeypatch.setattr(oracle, "moore_round", bad_round)
+    r = oracle.moore(A.delta, A.accept, history=True)
+    ok = all(oracle.is_refinement(c, p) for p, c in zip(r.history, r.history[1:]))
+    assert not ok or r.rounds_changed != A.n - 2
+
+
+def test_pins_catch_wrong_leader(monkeypatch):
+    """naivePR that compares q's successor with the leader itself (instead of the
+    leader's successor) must fail the Hopcroft pin."""
+    A = dfagen.random_dfa(300, 2, 0.5, 7)
+    h = oracle.hopcroft(A.delta, A.accept)
+    monkeypatch.setattr(oracle, "naive_differs", lambda d, block: block[d] != block[block])
+    assert not np.array_equal(oracle.naive_pr(A.delta, A.accept, max_rounds=3 * A.n).block, h)
+
+
+def test_pins_catch_broken_closure():
+    """A closure that squares the wrong row fails the repeated-application pin."""
+    A = dfagen.random_dfa(64, 2, 0.5, 4)
+    T = oracle.closure(A.delta)
+    L = oracle.closure_levels(64)
+    broken = T.copy()
+    broken[0 * (L + 1) + 2] = T[0 * (L + 1) + 1][T[1 * (L + 1) + 1]]   # mixes letters
+    cur = np.arange(64)
+    for _ in range(4):
+        cur = A.delta[0][cur]
+    assert np.array_equal(T[2], cur) and not np.array_equal(broken[2], cur)
