@@ -1,0 +1,308 @@
+"""Benchmark of the DFA partition-refinement hot path on GB300.
+
+One step = one dfa_minimise call (signature refinement, every round until the
+fixpoint, plus canonical numbering) on the 2^24-state, 4-letter random DFA
+(uniform uint32 targets, acceptance Bernoulli(0.5), seed 2), inputs resident
+in HBM.  The metric is transitions refined per second, n*|Σ|*rounds / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one process per GPU): every rank refines its own copy of the
+workload (independent problems, no collective on the data path); the value
+is the sum over ranks divided by the slowest rank's time ("weak" scaling).
+
+--impl reference times the CPU oracle (numpy, the machine's host cores) on a
+bounded sample of the same workload: one refinement round per step.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="random_dfa_n2^24_k4", n=1 << 24, k=4, p_accept=0.5, seed=2)
+METRIC = "transitions refined/sec (n*|Sigma|*rounds/s)"
+UNIT = "transitions/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the CPU-oracle leg (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = float(p[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(A, seconds_hint=True):
+    """The oracle as it stands, one Moore round on the full workload (a bounded sample)."""
+    import numpy as np
+    import oracle
+    block = oracle.initial_partition(A.accept)
+    t = time.perf_counter()
+    oracle.moore_round(A.delta, block)
+    dt = time.perf_counter() - t
+    n, k = A.n, A.k
+    return {"value": n * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one signature-refinement round of the numpy oracle on the full {n}-state, {k}-letter DFA "
+                      f"({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import dfagen
+    A = dfagen.random_dfa(WORKLOAD["n"], WORKLOAD["k"], WORKLOAD["p_accept"], WORKLOAD["seed"])
+    import oracle
+    block = oracle.initial_partition(A.accept)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        oracle.moore_round(A.delta, block)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = A.n * A.k * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": dict(WORKLOAD, parallelism="cpu", step="one oracle refinement round"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one signature-refinement round per step on the full workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    import dfagen
+    import paper_2508_20735_gb300 as g
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    g.build()
+
+    A = dfagen.random_dfa(WORKLOAD["n"], WORKLOAD["k"], WORKLOAD["p_accept"], WORKLOAD["seed"])
+    n, k = A.n, A.k
+    d_delta = torch.from_numpy(A.delta.view(np.int32)).cuda()
+    d_acc = torch.from_numpy(A.accept).cuda()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    dd, keep = g.make_dfa(d_delta, d_acc)
+    opts = g.make_opts("moore")
+    ws_bytes = g.dfa_workspace_size(dd, opts)
+    ws = g._workspace(ws_bytes)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    def step():
+        st, res = g.dfa_minimise(dd, opts, out.data_ptr(), ws.data_ptr(), ws_bytes, sptr)
+        if st != 0:
+            raise RuntimeError(f"dfa_minimise failed: {st} {g.last_error()}")
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rounds = []
+    dev_ns = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+            rounds.append(res.rounds_executed)
+            dev_ns.append(res.device_ns)
+        ev1.record(stream)
+        barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    trans = n * k * sum(rounds)
+    value = trans * world / (elapsed_ms * 1e-3)
+    ms_per_step = elapsed_ms / args.steps
+
+    # roofline of the refinement kernel: (4k+8)*n algorithmic bytes per round
+    kernel_s = statistics.mean(dev_ns) * 1e-9
+    algo_bytes = (4 * k + 8) * n * statistics.mean(rounds)
+    peak, peak_kind = peaks()
+    achieved = algo_bytes / kernel_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "traffic": None, "kernel": "dfa::moore_kernel",
+                "algorithmic_bytes_per_launch": algo_bytes, "kernel_ms": kernel_s * 1e3}
+    prof = os.path.join(ROOT, "profiles", "moore_kernel_random_n2p24_k4.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                pj = json.load(f)
+            if pj.get("kernel_source_hash") == kernel_source_hash():
+                roofline["traffic"] = pj["dram_bytes_per_launch"]
+        except Exception:
+            pass
+
+    # end to end through the same C call with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_delta = torch.from_numpy(A.delta.view(np.int32)).pin_memory()
+        h_acc = torch.from_numpy(A.accept).pin_memory()
+        h_out = torch.empty(n, dtype=torch.int32).pin_memory()
+        hd, hkeep = g.make_dfa(h_delta, h_acc)
+        hws_bytes = g.dfa_workspace_size(hd, opts)
+        hws = g._workspace(hws_bytes)
+
+        def hstep():
+            st, r = g.dfa_minimise(hd, opts, h_out.data_ptr(), hws.data_ptr(), hws_bytes, sptr)
+            if st != 0:
+                raise RuntimeError(f"dfa_minimise (host buffers) failed: {st} {g.last_error()}")
+            return r
+
+        for _ in range(max(1, args.warmup)):
+            hstep()
+        barrier()
+        t0 = time.perf_counter()
+        er = []
+        for _ in range(args.steps):
+            er.append(hstep().rounds_executed)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": n * k * sum(er) * world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_delta.numel() * 4 + h_acc.numel()),
+               "d2h_bytes_per_step": int(h_out.numel() * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(A)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": dict(WORKLOAD, algo="moore (signature refinement)", rounds=rounds[-1],
+                               l2="inputs larger than L2 (delta 256 MiB)",
+                               parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps,
+                "roofline": roofline, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def kernel_source_hash() -> str:
+    """Hash of the kernel sources, tying a committed ncu traffic figure to the code it measured."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2508_20735_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * dfa.h -- C ABI of the GB300 DFA partition-refinement library (libdfa_gb300.so).
+ *
+ * Problem statement (Section 2 of the paper): a DFA A = (Q, Σ, δ, F, q0) with
+ * states Q = {0..n-1} and letters Σ = {0..k-1}.  Minimisation identifies the
+ * DFA with the fewest states and the same language; on the hot path it is the
+ * coarsest partition of Q that respects F and is a congruence for δ ("the
+ * coarsest set partition problem", Section 2).  Equivalence asks L(A) = L(B)
+ * (Section 4).
+ *
+ * Representation (Section 2, "Representation"): δ is k arrays of length n,
+ * letter-major, delta[a*n + q] = δ(q, a), as uint32.  accept[q] != 0 iff q ∈ F.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Memory: every array argument may be a device pointer or a host pointer
+ *    (pageable or pinned); the library asks the CUDA runtime which it is.
+ *    Host inputs are copied into the workspace and host outputs are copied
+ *    back, all on `stream`.  The caller owns all inputs, outputs and the
+ *    workspace; the library keeps no pointer after a call returns.
+ *  - Workspace: the minimise, batch and equivalence calls never allocate
+ *    device memory.  The caller passes `workspace` (device memory, 256-byte
+ *    aligned) of at least the size the matching *_workspace_size call returns.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream-ordered and synchronise `stream` once before
+ *    returning, so `res`, verdicts and host outputs are valid on return.
+ *  - Errors: calls return a dfa_status and never abort.  dfa_last_error()
+ *    gives a thread-local message for the last failing call on this thread.
+ *    DFA_EINVAL covers n = 0, start >= n, a transition target >= n (detected
+ *    on the device), k_A != k_B for equivalence, and a workspace that is too
+ *    small.
+ *  - Limits: 1 <= n <= DFA_MAX_STATES; 0 <= k <= DFA_MAX_LETTERS (k = 0 gives
+ *    the partition {F, Q\F}).  All arithmetic is exact integer.
+ *  - Output: block_out[q] is q's block; blocks are numbered 0..B-1 in
+ *    increasing order of their smallest state (canonical numbering), so two
+ *    runs agree bit for bit whenever their partitions agree.
+ */
+#ifndef DFA_GB300_H
+#define DFA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DFA_MAX_STATES 0x7FFFFFFFu
+#define DFA_MAX_LETTERS 4096u
+
+/* One DFA.  Pointers are device or host pointers (see conventions). */
+typedef struct dfa_t {
+  uint32_t n;              /* number of states */
+  uint32_t k;              /* number of letters */
+  const uint32_t *delta;   /* k*n targets, delta[a*n + q] = δ(q, a) */
+  const uint8_t *accept;   /* n bytes, nonzero = accepting */
+  uint32_t start;          /* initial state; used by equivalence, ignored by minimise */
+} dfa_t;
+
+typedef enum dfa_status {
+  DFA_OK = 0,
+  DFA_EINVAL = -1,        /* bad argument, bad transition target or workspace too small */
+  DFA_ENOMEM = -2,        /* the server's HBM budget cannot hold a request */
+  DFA_ECUDA = -3,         /* a CUDA runtime call failed (message in dfa_last_error) */
+  DFA_ETIMEOUT = -4,      /* a device-side wait or the call's time limit ran out */
+  DFA_EMAXROUNDS = -5,    /* opts.max_rounds rounds ran without reaching the fixpoint */
+  DFA_EBUSY = -6,         /* server: request not finished yet (poll) */
+  DFA_ECANCELLED = -7     /* server: request was cancelled */
+} dfa_status;
+
+typedef enum dfa_algo {
+  DFA_ALGO_MOORE = 0,     /* signature refinement, Section 3.3 / Algorithm 4 (sortPR's result) */
+  DFA_ALGO_NAIVE = 1,     /* leader-election refinement, Section 3.2 / Algorithm 2 */
+  DFA_ALGO_TRANS = 2      /* partial transitive closure + naivePR, Section 3.4 / Algorithm 5 */
+} dfa_algo;
+
+/* Flags for dfa_opts.flags */
+#define DFA_FLAG_EARLY_EXIT 0x1u   /* equivalence: stop once the start states separate */
+
+typedef struct dfa_opts {
+  int32_t algo;            /* dfa_algo */
+  uint32_t max_rounds;     /* 0 = no limit; otherwise DFA_EMAXROUNDS after this many rounds */
+  uint64_t timeout_ns;     /* 0 = library default (600 s); limit on the whole call's device work */
+  int32_t schedule;        /* -1 = autotune / default; >= 0 selects a kernel schedule (batch) */
+  uint32_t flags;          /* DFA_FLAG_* */
+} dfa_opts;
+
+/* Round counts follow Algorithm 4's loop: rounds_changed counts rounds whose
+ * block count grew; rounds_executed also counts the final round that finds the
+ * count unchanged (the fixpoint test).  For naivePR/transPR a round is one
+ * iteration of Algorithm 2's while-loop, the last one finding no split. */
+typedef struct dfa_result {
+  uint32_t num_blocks;
+  uint32_t rounds_changed;
+  uint32_t rounds_executed;
+  int32_t status;          /* dfa_status of this DFA */
+  uint64_t device_ns;      /* device time of the refinement kernel(s) */
+} dfa_result;
+
+/* ---------------------------------------------------------------- minimise */
+
+/* Bytes of workspace dfa_minimise needs for this DFA and options (0 on bad arguments). */
+size_t dfa_workspace_size(const dfa_t *dfa, const dfa_opts *opts);
+
+/* Coarsest partition of all n states of `dfa` (unreachable states are kept;
+ * Section 2 treats their removal as a separate pre-processing step).
+ * block_out: n uint32 (device or host).  res: host struct.  opts may be NULL
+ * (Moore, no round limit, default time limit). */
+int dfa_minimise(const dfa_t *dfa, const dfa_opts *opts, uint32_t *block_out, dfa_result *res,
+                 void *workspace, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- batch */
+
+/* Workspace bytes for dfa_minimise_batch over `count` DFAs (host array of dfa_t). */
+size_t dfa_batch_workspace_size(const dfa_t *dfas, uint32_t count, const dfa_opts *opts);
+
+/* Refines `count` independent DFAs in one persistent launch.  block_out holds
+ * sum(n_i) entries, DFA i's blocks at offset sum_{j<i} n_j, numbered within
+ * DFA i.  res[i] (host array of count) equals what dfa_minimise reports for DFA
+ * i alone (partition and round counts; device_ns is the whole batch's time).
+ * The DFAs' arrays may live anywhere (host or device), independently. */
+int dfa_minimise_batch(const dfa_t *dfas, uint32_t count, const dfa_opts *opts, uint32_t *block_out,
+                       dfa_result *res, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- equivalence */
+
+/* Workspace bytes for dfa_equivalent on this pair. */
+size_t dfa_equivalent_workspace_size(const dfa_t *a, const dfa_t *b, const dfa_opts *opts);
+
+/* L(A) = L(B)?  Decided by refining the disjoint union A ⊎ B (B's states
+ * offset by n_A) and comparing the blocks of the two start states (Section 4:
+ * equivalence by minimisation).  Requires k_A = k_B.  *equivalent is set to 1
+ * or 0.  res describes the union's refinement; with DFA_FLAG_EARLY_EXIT the
+ * refinement stops at the first round that separates the start states, and
+ * res->rounds_executed is then the length of a shortest word that A and B
+ * disagree on. */
+int dfa_equivalent(const dfa_t *a, const dfa_t *b, const dfa_opts *opts, int *equivalent,
+                   dfa_result *res, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct dfa_server dfa_server;
+
+#define DFA_REQ_MINIMISE 0
+#define DFA_REQ_EQUIVALENT 1
+
+/* A server owns one device arena of hbm_budget_bytes (allocated once here) and
+ * a host thread that admits queued requests while arena space and one of
+ * max_slots slots are free, and refines all admitted requests together, one
+ * round at a time (continuous batching). */
+int dfa_serve_create(dfa_server **out, size_t hbm_budget_bytes, uint32_t max_slots, int device);
+
+/* Queues a request; the DFAs are copied in before this returns, so the caller
+ * may free them.  `b` is NULL for DFA_REQ_MINIMISE.  *ticket identifies it.
+ * DFA_ENOMEM if the request can never fit the budget. */
+int dfa_serve_submit(dfa_server *s, int kind, const dfa_t *a, const dfa_t *b, const dfa_opts *opts,
+                     uint64_t *ticket);
+
+/* DFA_EBUSY while the request is queued or running; DFA_OK (or the request's
+ * error) once finished, filling res, *equivalent (equivalence requests) and,
+ * if block_out is non-NULL, the partition (host memory, n or n_A + n_B
+ * entries).  A finished ticket is released by the first successful poll/wait. */
+int dfa_serve_poll(dfa_server *s, uint64_t ticket, dfa_result *res, int *equivalent, uint32_t *block_out);
+
+/* As dfa_serve_poll, but blocks up to timeout_ns (0 = forever). */
+int dfa_serve_wait(dfa_server *s, uint64_t ticket, uint64_t timeout_ns, dfa_result *res, int *equivalent,
+                   uint32_t *block_out);
+
+/* Latency percentiles (submit to completion) and throughput of finished requests. */
+int dfa_serve_stats(dfa_server *s, double *p50_us, double *p99_us, double *throughput_rps);
+
+/* Cancels outstanding requests, joins the thread and frees the arena. */
+int dfa_serve_destroy(dfa_server *s);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Thread-local message describing the last failing call on this thread. */
+const char *dfa_last_error(void);
+
+/* Library version string. */
+const char *dfa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFA_GB300_H */

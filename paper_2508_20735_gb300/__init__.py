@@ -1,0 +1,293 @@
+"""Python binding of libdfa_gb300.so (the C ABI declared in include/dfa.h).
+
+Argument marshalling only: every step of the refinement runs in the library's
+CUDA kernels.  The functions named ``dfa_*`` mirror the C calls one to one;
+:func:`minimise`, :func:`equivalent` and :func:`minimise_batch` are thin
+conveniences that accept torch tensors or numpy arrays, allocate the workspace
+with PyTorch's caching allocator and pass torch's current CUDA stream.
+
+There is no CPU fallback: if the shared library is missing or cannot be loaded
+the import of any entry point raises :class:`LibraryMissing`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_size_t, c_uint32, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdfa_gb300.so")
+
+DFA_OK, DFA_EINVAL, DFA_ENOMEM, DFA_ECUDA, DFA_ETIMEOUT, DFA_EMAXROUNDS, DFA_EBUSY, DFA_ECANCELLED = 0, -1, -2, -3, -4, -5, -6, -7
+STATUS_NAMES = {0: "DFA_OK", -1: "DFA_EINVAL", -2: "DFA_ENOMEM", -3: "DFA_ECUDA", -4: "DFA_ETIMEOUT",
+                -5: "DFA_EMAXROUNDS", -6: "DFA_EBUSY", -7: "DFA_ECANCELLED"}
+ALGOS = {"moore": 0, "naive": 1, "trans": 2}
+DFA_FLAG_EARLY_EXIT = 0x1
+DFA_REQ_MINIMISE, DFA_REQ_EQUIVALENT = 0, 1
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class DfaError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class DfaT(ctypes.Structure):
+    _fields_ = [("n", c_uint32), ("k", c_uint32), ("delta", c_void_p), ("accept", c_void_p), ("start", c_uint32)]
+
+
+class DfaOpts(ctypes.Structure):
+    _fields_ = [("algo", c_int32), ("max_rounds", c_uint32), ("timeout_ns", c_uint64), ("schedule", c_int32),
+                ("flags", c_uint32)]
+
+
+class DfaResult(ctypes.Structure):
+    _fields_ = [("num_blocks", c_uint32), ("rounds_changed", c_uint32), ("rounds_executed", c_uint32),
+                ("status", c_int32), ("device_ns", c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+# (name, restype, argtypes) of every C entry point
+_SIGS = [
+    ("dfa_workspace_size", c_size_t, [POINTER(DfaT), POINTER(DfaOpts)]),
+    ("dfa_minimise", c_int, [POINTER(DfaT), POINTER(DfaOpts), c_void_p, POINTER(DfaResult), c_void_p, c_size_t, c_void_p]),
+    ("dfa_batch_workspace_size", c_size_t, [POINTER(DfaT), c_uint32, POINTER(DfaOpts)]),
+    ("dfa_minimise_batch", c_int, [POINTER(DfaT), c_uint32, POINTER(DfaOpts), c_void_p, POINTER(DfaResult), c_void_p,
+                                   c_size_t, c_void_p]),
+    ("dfa_equivalent_workspace_size", c_size_t, [POINTER(DfaT), POINTER(DfaT), POINTER(DfaOpts)]),
+    ("dfa_equivalent", c_int, [POINTER(DfaT), POINTER(DfaT), POINTER(DfaOpts), POINTER(c_int), POINTER(DfaResult),
+                               c_void_p, c_size_t, c_void_p]),
+    ("dfa_serve_create", c_int, [POINTER(c_void_p), c_size_t, c_uint32, c_int]),
+    ("dfa_serve_submit", c_int, [c_void_p, c_int, POINTER(DfaT), POINTER(DfaT), POINTER(DfaOpts), POINTER(c_uint64)]),
+    ("dfa_serve_poll", c_int, [c_void_p, c_uint64, POINTER(DfaResult), POINTER(c_int), c_void_p]),
+    ("dfa_serve_wait", c_int, [c_void_p, c_uint64, c_uint64, POINTER(DfaResult), POINTER(c_int), c_void_p]),
+    ("dfa_serve_stats", c_int, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
+    ("dfa_serve_destroy", c_int, [c_void_p]),
+    ("dfa_last_error", ctypes.c_char_p, []),
+    ("dfa_version", ctypes.c_char_p, []),
+]
+
+
+def lib():
+    """The loaded shared library (raises LibraryMissing if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LibraryMissing(f"{LIB_PATH} not found; build it with __graft_entry__.build() "
+                                 "or python paper_2508_20735_gb300/_build.py")
+        try:
+            L = ctypes.CDLL(LIB_PATH)
+        except OSError as e:
+            raise LibraryMissing(f"cannot load {LIB_PATH}: {e}") from e
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)
+
+
+def last_error() -> str:
+    return lib().dfa_last_error().decode()
+
+
+def _check(status: int):
+    if status not in (DFA_OK,):
+        raise DfaError(status, last_error())
+
+
+# ----------------------------------------------------------------- marshalling
+
+def _ptr(x):
+    """Address of a torch tensor or numpy array (kept alive by the caller)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _contig(x, np_dtype):
+    """Contiguous 32-bit (np_dtype uint32) or 8-bit (uint8) view of x."""
+    if hasattr(x, "data_ptr"):
+        import torch
+        if np_dtype == np.uint32:
+            ok = (torch.int32, getattr(torch, "uint32", torch.int32))   # same bits
+            if x.dtype not in ok:
+                x = x.to(torch.int32)
+        elif x.dtype != torch.uint8:
+            x = x.to(torch.uint8)
+        return x.contiguous()
+    return np.ascontiguousarray(x, dtype=np_dtype)
+
+
+def make_dfa(delta, accept, start: int = 0) -> tuple[DfaT, tuple]:
+    """A dfa_t for arrays delta (k, n) of 32-bit targets and accept (n,) bytes;
+    returns the struct and the arrays it points into (keep them alive)."""
+    delta = _contig(delta, np.uint32)
+    accept = _contig(accept, np.uint8)
+    k, n = int(delta.shape[0]), int(delta.shape[1])
+    if int(accept.shape[0]) != n:
+        raise ValueError("delta must have shape (k, n) matching accept (n,)")
+    d = DfaT(n, k, _ptr(delta) if k > 0 and n > 0 else None, _ptr(accept), int(start))
+    return d, (delta, accept)
+
+
+def make_opts(algo="moore", max_rounds=0, timeout_ns=0, schedule=-1, flags=0) -> DfaOpts:
+    a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    return DfaOpts(a, int(max_rounds), int(timeout_ns), int(schedule), int(flags))
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _workspace(nbytes: int, device=None):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+# ----------------------------------------------------------------- C entry points
+
+def dfa_workspace_size(dfa: DfaT, opts: DfaOpts | None = None) -> int:
+    return int(lib().dfa_workspace_size(ctypes.byref(dfa), ctypes.byref(opts) if opts else None))
+
+
+def dfa_minimise(dfa: DfaT, opts: DfaOpts | None, block_out_ptr: int, workspace_ptr: int, ws_bytes: int,
+                 stream: int | None) -> tuple[int, DfaResult]:
+    res = DfaResult()
+    st = lib().dfa_minimise(ctypes.byref(dfa), ctypes.byref(opts) if opts else None, block_out_ptr,
+                            ctypes.byref(res), workspace_ptr, ws_bytes, stream)
+    return st, res
+
+
+def dfa_equivalent_workspace_size(a: DfaT, b: DfaT, opts: DfaOpts | None = None) -> int:
+    return int(lib().dfa_equivalent_workspace_size(ctypes.byref(a), ctypes.byref(b),
+                                                   ctypes.byref(opts) if opts else None))
+
+
+def dfa_equivalent(a: DfaT, b: DfaT, opts: DfaOpts | None, workspace_ptr: int, ws_bytes: int,
+                   stream: int | None) -> tuple[int, bool, DfaResult]:
+    res = DfaResult()
+    eq = c_int(-1)
+    st = lib().dfa_equivalent(ctypes.byref(a), ctypes.byref(b), ctypes.byref(opts) if opts else None,
+                              ctypes.byref(eq), ctypes.byref(res), workspace_ptr, ws_bytes, stream)
+    return st, bool(eq.value == 1), res
+
+
+def dfa_batch_workspace_size(dfas, opts: DfaOpts | None = None) -> int:
+    arr = (DfaT * len(dfas))(*dfas)
+    return int(lib().dfa_batch_workspace_size(arr, len(dfas), ctypes.byref(opts) if opts else None))
+
+
+def dfa_minimise_batch(dfas, opts: DfaOpts | None, block_out_ptr: int, workspace_ptr: int, ws_bytes: int,
+                       stream: int | None):
+    arr = (DfaT * len(dfas))(*dfas)
+    res = (DfaResult * len(dfas))()
+    st = lib().dfa_minimise_batch(arr, len(dfas), ctypes.byref(opts) if opts else None, block_out_ptr, res,
+                                  workspace_ptr, ws_bytes, stream)
+    return st, list(res)
+
+
+# ----------------------------------------------------------------- conveniences
+
+def minimise(delta, accept, algo="moore", max_rounds=0, timeout_ns=0, out=None, workspace=None, stream=None,
+             check=True, schedule=-1):
+    """Coarsest partition of the DFA given by delta (k, n) and accept (n,).
+
+    Arrays may be CUDA tensors, CPU tensors or numpy arrays.  The output has the
+    input's kind (CUDA tensor in -> CUDA tensor out; otherwise numpy).
+    Returns (block, DfaResult)."""
+    d, keep = make_dfa(delta, accept)
+    o = make_opts(algo, max_rounds, timeout_ns, schedule)
+    on_dev = _is_cuda(keep[1])
+    if out is None:
+        if on_dev:
+            import torch
+            out = torch.empty(d.n, dtype=torch.int32, device=keep[1].device)
+        else:
+            out = np.empty(d.n, dtype=np.uint32)
+    need = dfa_workspace_size(d, o)
+    if need == 0:
+        raise DfaError(DFA_EINVAL, last_error())
+    if workspace is None:
+        workspace = _workspace(need)
+    st, res = dfa_minimise(d, o, _ptr(out), _ptr(workspace), int(workspace.numel()), _stream(stream))
+    if check and st not in (DFA_OK,):
+        raise DfaError(st, last_error())
+    res.call_status = st
+    return out, res
+
+
+def equivalent(A, B, early_exit=False, timeout_ns=0, workspace=None, stream=None, check=True):
+    """L(A) = L(B)?  A and B are (delta, accept, start) triples.  Returns (bool, DfaResult)."""
+    a, ka = make_dfa(A[0], A[1], A[2])
+    b, kb = make_dfa(B[0], B[1], B[2])
+    o = make_opts("moore", 0, timeout_ns, flags=DFA_FLAG_EARLY_EXIT if early_exit else 0)
+    need = dfa_equivalent_workspace_size(a, b, o)
+    if need == 0:
+        raise DfaError(DFA_EINVAL, last_error() or "bad arguments")
+    if workspace is None:
+        workspace = _workspace(need)
+    st, eq, res = dfa_equivalent(a, b, o, _ptr(workspace), int(workspace.numel()), _stream(stream))
+    if check and st != DFA_OK:
+        raise DfaError(st, last_error())
+    res.call_status = st
+    return eq, res
+
+
+def minimise_batch(dfas, algo="moore", max_rounds=0, timeout_ns=0, schedule=-1, out=None, workspace=None,
+                   stream=None, check=True):
+    """Refine a list of (delta, accept) pairs in one launch.  Returns (blocks, [DfaResult])."""
+    structs, keep = [], []
+    for item in dfas:
+        d, kk = make_dfa(item[0], item[1])
+        structs.append(d)
+        keep.append(kk)
+    o = make_opts(algo, max_rounds, timeout_ns, schedule)
+    total = sum(s.n for s in structs)
+    if out is None:
+        import torch
+        out = torch.empty(total, dtype=torch.int32, device="cuda")
+    need = dfa_batch_workspace_size(structs, o)
+    if need == 0:
+        raise DfaError(DFA_EINVAL, last_error() or "bad arguments")
+    if workspace is None:
+        workspace = _workspace(need)
+    st, res = dfa_minimise_batch(structs, o, _ptr(out), _ptr(workspace), int(workspace.numel()), _stream(stream))
+    if check and st != DFA_OK:
+        raise DfaError(st, last_error())
+    return out, res
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/dfa.h declares (used by the ABI tests)."""
+    import re
+    path = os.path.join(os.path.dirname(_HERE), "include", "dfa.h")
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dfa_[a-z_0-9]+)\s*\(", src)))

@@ -1,0 +1,246 @@
+// C ABI (include/dfa.h): argument checks, workspace layout, host staging and
+// launches.  Every step of the refinement runs in the kernels of this library.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/dfa.h"
+#include "api_util.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace dfa {
+
+static thread_local std::string g_err;
+
+int fail(int status, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(DFA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void *p) {
+  if (p == nullptr) return true;
+  cudaPointerAttributes at;
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+uint32_t ceil_log2(uint64_t x) {
+  uint32_t b = 0;
+  while ((1ull << b) < x) ++b;
+  return b;
+}
+
+dfa_opts default_opts(const dfa_opts *o) {
+  dfa_opts d;
+  memset(&d, 0, sizeof d);
+  d.algo = DFA_ALGO_MOORE;
+  d.schedule = -1;
+  if (o) d = *o;
+  if (d.timeout_ns == 0) d.timeout_ns = 600ull * 1000000000ull;
+  return d;
+}
+
+int check_dfa(const dfa_t *d, const char *name) {
+  if (!d) return fail(DFA_EINVAL, "%s is NULL", name);
+  if (d->n == 0) return fail(DFA_EINVAL, "%s: n = 0", name);
+  if (d->n > DFA_MAX_STATES) return fail(DFA_EINVAL, "%s: n = %u exceeds %u", name, d->n, DFA_MAX_STATES);
+  if (d->k > DFA_MAX_LETTERS) return fail(DFA_EINVAL, "%s: k = %u exceeds %u", name, d->k, DFA_MAX_LETTERS);
+  if (d->start >= d->n) return fail(DFA_EINVAL, "%s: start %u >= n %u", name, d->start, d->n);
+  if (d->k > 0 && d->delta == nullptr) return fail(DFA_EINVAL, "%s: delta is NULL", name);
+  if (d->accept == nullptr) return fail(DFA_EINVAL, "%s: accept is NULL", name);
+  return DFA_OK;
+}
+
+// ------------------------------------------------------------------ Moore workspace
+static constexpr size_t kMaxGrid = 8192;
+
+MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_accept, bool stage_out) {
+  MooreLayout L{};
+  L.log2S = ceil_log2(n * 2 < 64 ? 64 : n * 2);
+  const StagePlan p1 = make_plan(k, 1), pr = make_plan(k, L.log2S);
+  L.plan1 = p1;
+  L.planr = pr;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  L.ctrl = take(sizeof(Ctrl));
+  L.table = take(((size_t)1 << L.log2S) * 16);
+  L.lab0 = take(n * 4);
+  L.lab1 = take(n * 4);
+  L.tmp = (p1.stages > 1 || pr.stages > 1) ? take(n * 4) : SIZE_MAX;
+  L.minrep = take(((size_t)1 << L.log2S) * 4);
+  L.flag = take(n);
+  L.partials = take(kMaxGrid * 4);
+  L.delta = stage_delta ? take((size_t)k * n * 4) : SIZE_MAX;
+  L.accept = stage_accept ? take(n) : SIZE_MAX;
+  L.out = stage_out ? take(n * 4) : SIZE_MAX;
+  L.total = off;
+  return L;
+}
+
+// Runs the Moore kernel over a device-resident DFA (delta/accept are device
+// pointers) writing canonical blocks to out_dev.  Fills *ctrl_host.
+int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
+              const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
+              Ctrl *ctrl_host, uint32_t vec_ok) {
+  MooreArgs a{};
+  a.delta = delta_dev;
+  a.accept = accept_dev;
+  a.n = n;
+  a.k = k;
+  a.lab[0] = reinterpret_cast<uint32_t *>(ws + L.lab0);
+  a.lab[1] = reinterpret_cast<uint32_t *>(ws + L.lab1);
+  a.tmp = L.tmp == SIZE_MAX ? nullptr : reinterpret_cast<uint32_t *>(ws + L.tmp);
+  a.table = reinterpret_cast<u128 *>(ws + L.table);
+  a.log2S = L.log2S;
+  a.minrep = reinterpret_cast<uint32_t *>(ws + L.minrep);
+  a.flag = reinterpret_cast<uint8_t *>(ws + L.flag);
+  a.partials = reinterpret_cast<uint32_t *>(ws + L.partials);
+  a.out = out_dev;
+  a.ctrl = reinterpret_cast<Ctrl *>(ws + L.ctrl);
+  a.plan1 = L.plan1;
+  a.planr = L.planr;
+  a.ebits = L.plan1.ebits < L.planr.ebits ? L.plan1.ebits : L.planr.ebits;
+  a.max_rounds = o.max_rounds;
+  a.timeout_ns = o.timeout_ns;
+  a.barrier_ns = o.timeout_ns < 5000000000ull ? o.timeout_ns : 5000000000ull;
+  a.vec = vec_ok;
+  a.stream_delta = ((uint64_t)k * n * 4 > (64ull << 20)) ? 1u : 0u;
+  if (track) {
+    a.track_pair = 1;
+    a.sep_a = track->a;
+    a.sep_b = track->b;
+    a.early_exit = track->early_exit;
+  }
+  cudaError_t e = cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ctrl)");
+  LaunchInfo li{};
+  e = moore_grid(a.vec, &li);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if ((size_t)li.grid > kMaxGrid) return fail(DFA_ECUDA, "grid of %d blocks exceeds %zu", li.grid, kMaxGrid);
+  e = launch_moore(a, st, &li);
+  if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the refinement kernel");
+  e = cudaMemcpyAsync(ctrl_host, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(ctrl)");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "refinement kernel");
+  return DFA_OK;
+}
+
+int status_from_ctrl(const Ctrl &c) {
+  if (c.err & ERR_BAD_DELTA) return fail(DFA_EINVAL, "a transition target is >= n");
+  if (c.err & ERR_TIMEOUT) return fail(DFA_ETIMEOUT, "device-side wait or call time limit exceeded");
+  if (c.err & ERR_TABLE_FULL) return fail(DFA_ECUDA, "renumbering table overflow (internal error)");
+  if (c.maxed) return fail(DFA_EMAXROUNDS, "max_rounds reached before the fixpoint");
+  return DFA_OK;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// States per thread in the Moore kernel: `schedule` 1, 2 or 4 asks for that
+// width; otherwise 1 (measured fastest on GB300 for both deep-round and
+// bandwidth-bound inputs).  A width needs n divisible by it and aligned rows.
+uint32_t pick_vec(uint32_t n, uint32_t k, const void *delta, const void *accept, int32_t schedule) {
+  uint32_t want = (schedule == 1 || schedule == 2 || schedule == 4) ? (uint32_t)schedule : 1u;
+  while (want > 1) {
+    if (n % want == 0 && (k == 0 || aligned(delta, 4 * want)) && aligned(accept, want)) return want;
+    want >>= 1;
+  }
+  return 1;
+}
+
+}  // namespace dfa
+
+using namespace dfa;
+
+extern "C" {
+
+const char *dfa_last_error(void) { return g_err.c_str(); }
+
+const char *dfa_version(void) { return "dfa_gb300 0.1 (sm_103a)"; }
+
+size_t dfa_workspace_size(const dfa_t *d, const dfa_opts *opts) {
+  if (check_dfa(d, "dfa") != DFA_OK) return 0;
+  const dfa_opts o = default_opts(opts);
+  if (o.algo == DFA_ALGO_MOORE) {
+    const bool hd = d->k > 0 && !is_device_ptr(d->delta);
+    const bool ha = !is_device_ptr(d->accept);
+    return moore_layout(d->n, d->k, hd, ha, true).total;
+  }
+  return naive_workspace_size(d, o);
+}
+
+int dfa_minimise(const dfa_t *d, const dfa_opts *opts, uint32_t *block_out, dfa_result *res, void *workspace,
+                 size_t ws_bytes, void *stream) {
+  int rc = check_dfa(d, "dfa");
+  if (rc != DFA_OK) return rc;
+  if (!block_out) return fail(DFA_EINVAL, "block_out is NULL");
+  if (!workspace) return fail(DFA_EINVAL, "workspace is NULL");
+  if (!aligned(workspace, 256)) return fail(DFA_EINVAL, "workspace must be 256-byte aligned");
+  const dfa_opts o = default_opts(opts);
+  if (o.algo != DFA_ALGO_MOORE && o.algo != DFA_ALGO_NAIVE && o.algo != DFA_ALGO_TRANS)
+    return fail(DFA_EINVAL, "unknown algo %d", o.algo);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (o.algo != DFA_ALGO_MOORE) return run_naive_minimise(d, o, block_out, res, workspace, ws_bytes, st);
+
+  const bool hd = d->k > 0 && !is_device_ptr(d->delta);
+  const bool ha = !is_device_ptr(d->accept);
+  const bool ho = !is_device_ptr(block_out);
+  const MooreLayout L = moore_layout(d->n, d->k, hd, ha, true);
+  if (ws_bytes < L.total) return fail(DFA_EINVAL, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
+  char *ws = static_cast<char *>(workspace);
+  const uint32_t *delta = d->delta;
+  const uint8_t *accept = d->accept;
+  cudaError_t e;
+  if (hd) {
+    e = cudaMemcpyAsync(ws + L.delta, d->delta, (size_t)d->k * d->n * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy delta to device");
+    delta = reinterpret_cast<const uint32_t *>(ws + L.delta);
+  }
+  if (ha) {
+    e = cudaMemcpyAsync(ws + L.accept, d->accept, d->n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy accept to device");
+    accept = reinterpret_cast<const uint8_t *>(ws + L.accept);
+  }
+  uint32_t *out = ho ? reinterpret_cast<uint32_t *>(ws + L.out) : block_out;
+  const uint32_t vec_ok = pick_vec(d->n, d->k, delta, accept, o.schedule);
+  Ctrl c{};
+  rc = run_moore(delta, accept, d->n, d->k, out, L, ws, o, st, nullptr, &c, vec_ok);
+  if (rc != DFA_OK) return rc;
+  const int status = status_from_ctrl(c);
+  if (res) {
+    res->num_blocks = c.num_blocks;
+    res->rounds_changed = c.rounds_changed;
+    res->rounds_executed = c.rounds_executed;
+    res->status = status;
+    res->device_ns = c.t_end - c.t_start;
+  }
+  if (status != DFA_OK && status != DFA_EMAXROUNDS) return status;
+  if (ho) {
+    e = cudaMemcpyAsync(block_out, out, (size_t)d->n * 4, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy blocks to host");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy blocks to host");
+  }
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Host helpers shared by the C-ABI translation units.  Not part of the public ABI.
+#pragma once
+#include <cstdarg>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/dfa.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace dfa {
+
+// Byte offsets of the Moore kernel's buffers inside a caller's workspace
+// (SIZE_MAX = absent).
+struct MooreLayout {
+  uint32_t log2S;
+  StagePlan plan1, planr;
+  size_t ctrl, table, lab0, lab1, tmp, minrep, flag, partials, delta, accept, out, total;
+};
+
+// Equivalence by union: the two start states whose blocks are compared.
+struct PairTrack {
+  uint32_t a, b, early_exit;
+};
+
+int fail(int status, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+bool is_device_ptr(const void *p);
+uint32_t ceil_log2(uint64_t x);
+dfa_opts default_opts(const dfa_opts *o);
+int check_dfa(const dfa_t *d, const char *name);
+bool aligned(const void *p, size_t a);
+uint32_t pick_vec(uint32_t n, uint32_t k, const void *delta, const void *accept, int32_t schedule);
+MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_accept, bool stage_out);
+int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
+              const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
+              Ctrl *ctrl_host, uint32_t vec_ok);
+int status_from_ctrl(const Ctrl &c);
+
+// naivePR / transPR (naive.cu)
+size_t naive_workspace_size(const dfa_t *d, const dfa_opts &o);
+int run_naive_minimise(const dfa_t *d, const dfa_opts &o, uint32_t *block_out, dfa_result *res, void *workspace,
+                       size_t ws_bytes, cudaStream_t st);
+
+// disjoint union helper (equiv.cu)
+cudaError_t launch_offset_targets(uint32_t *delta_u, uint32_t n_u, uint32_t k, uint32_t first, uint32_t count,
+                                  uint32_t offset, uint32_t *err, cudaStream_t st);
+
+}  // namespace dfa

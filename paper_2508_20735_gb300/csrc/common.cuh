@@ -1,0 +1,419 @@
+// Device primitives shared by the refinement kernels (sm_103a).
+//
+//  * 128-bit keys and the exact open-addressing table used to renumber blocks
+//    (Section 3.3 renumbers by sorting; the hashing alternative it cites is
+//    used here, with exact keys so that no two signatures ever merge).
+//  * A grid barrier for persistent cooperative kernels whose every wait is
+//    bounded by %globaltimer, so a lost block turns into an error status, not
+//    a hang.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dfa {
+
+// ----------------------------------------------------------------- errors
+enum : uint32_t {
+  ERR_BAD_DELTA = 1u,      // a transition target >= n
+  ERR_TIMEOUT = 2u,        // a barrier wait or the call's deadline ran out
+  ERR_TABLE_FULL = 4u,     // no free slot (cannot happen with the sizing used)
+};
+
+// Control block at the start of every workspace (zeroed by the host before launch).
+struct Ctrl {
+  uint32_t bar_count;      // grid barrier: arrivals in the current generation
+  uint32_t bar_gen;        // grid barrier: generation
+  uint32_t err;            // ERR_* bits
+  uint32_t cnt[3];         // per-round new-block counts (ring of three)
+  uint32_t seen_acc;       // some state accepting
+  uint32_t seen_rej;       // some state rejecting
+  uint32_t num_blocks;
+  uint32_t rounds_changed;
+  uint32_t rounds_executed;
+  uint32_t flag;           // naivePR: some state split this round (ring use in kernels)
+  uint32_t flag2[3];
+  uint32_t sep_round;      // equivalence: round that separated the start states (or ~0)
+  uint32_t verdict;        // equivalence: 1 = same block
+  uint32_t maxed;          // stopped at opts.max_rounds (not an error for the barrier)
+  uint32_t pad;
+  unsigned long long t_start, t_end;
+  unsigned long long deadline;  // absolute %globaltimer value
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Grid-wide barrier for a cooperative launch.  Returns false (in every thread of
+// the block) if the error word is set or the wait exceeded `limit_ns`; the
+// kernel must then stop.  The last block to arrive also checks the call's
+// deadline, so the decision to stop is the same in every block.
+__device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long limit_ns) {
+  __shared__ uint32_t s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t ok = 1;
+    const uint32_t gen = ld_acquire(&c->bar_gen);
+    const uint32_t arrived = atom_add_acq_rel(&c->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      if (gtimer() > c->deadline) atomicOr(&c->err, ERR_TIMEOUT);
+      c->bar_count = 0;                       // nobody arrives again before gen moves on
+      st_release(&c->bar_gen, gen + 1);
+    } else {
+      const unsigned long long t0 = gtimer();
+      while (ld_acquire(&c->bar_gen) == gen) {
+        if (ld_relaxed(&c->err) != 0u) { ok = 0; break; }
+        if (gtimer() - t0 > limit_ns) { atomicOr(&c->err, ERR_TIMEOUT); ok = 0; break; }
+        __nanosleep(64);
+      }
+    }
+    if (ok && ld_acquire(&c->err) != 0u) ok = 0;
+    // gpu-scope acquire by this thread also invalidates the SM's L1, so weak
+    // loads issued by any thread of the block after the barrier see fresh data
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0u;
+}
+
+// ----------------------------------------------------------------- L2 cache policies
+// The label array gathered every round is kept in L2 (evict_last); streamed
+// inputs, table probes and freshly written labels are evicted first, so the
+// random traffic of a large renumbering table does not push the labels out.
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_u32_hint(const uint32_t *p, unsigned long long pol) {
+  uint32_t v;
+  asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_v4_stream(const uint32_t *p, unsigned long long pol) {
+  uint4 v;
+  asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_u32_stream(const uint32_t *p, unsigned long long pol) {
+  uint32_t v;
+  asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_v4_hint(uint32_t *p, uint4 v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_u32_hint(uint32_t *p, uint32_t v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
+// ----------------------------------------------------------------- 128-bit keys
+struct __align__(16) u128 {
+  unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ bool eq128(u128 a, u128 b) { return a.lo == b.lo && a.hi == b.hi; }
+
+// OR value v (< 2^bits, bits <= 32) into key at bit offset `shift` (shift + bits <= 128).
+__device__ __forceinline__ void put_bits(u128 &k, uint32_t v, uint32_t shift) {
+  const unsigned long long x = v;
+  if (shift < 64) {
+    k.lo |= x << shift;
+    if (shift > 32) k.hi |= x >> (64 - shift);
+  } else {
+    k.hi |= x << (shift - 64);
+  }
+}
+
+// Weak 16-byte load as one vector instruction.  Caches move whole 32-byte
+// sectors, so the two halves come from the same write; the value may be stale.
+__device__ __forceinline__ u128 ld_b128_weak(const u128 *p) {
+  u128 r;
+  asm volatile(
+      "{\n\t.reg .b64 pol;\n\t"
+      "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+      "ld.global.L2::cache_hint.v2.u64 {%0, %1}, [%2], pol;\n\t}"
+      : "=l"(r.lo), "=l"(r.hi)
+      : "l"(p)
+      : "memory");
+  return r;
+}
+
+// 128-bit atomic load (single-copy atomic; never a torn mix of two writes).
+__device__ __forceinline__ u128 ld_b128_relaxed(const u128 *p) {
+  u128 r;
+  asm volatile(
+      "{\n\t.reg .b128 t;\n\t"
+      "ld.relaxed.gpu.global.b128 t, [%2];\n\t"
+      "mov.b128 {%0, %1}, t;\n\t}"
+      : "=l"(r.lo), "=l"(r.hi)
+      : "l"(p)
+      : "memory");
+  return r;
+}
+
+__device__ __forceinline__ u128 cas_b128(u128 *p, u128 cmp, u128 val) {
+  u128 r;
+  asm volatile(
+      "{\n\t.reg .b128 c, v, d;\n\t"
+      "mov.b128 c, {%2, %3};\n\t"
+      "mov.b128 v, {%4, %5};\n\t"
+      "atom.relaxed.gpu.global.cas.b128 d, [%6], c, v;\n\t"
+      "mov.b128 {%0, %1}, d;\n\t}"
+      : "=l"(r.lo), "=l"(r.hi)
+      : "l"(cmp.lo), "l"(cmp.hi), "l"(val.lo), "l"(val.hi), "l"(p)
+      : "memory");
+  return r;
+}
+
+// Finaliser of MurmurHash3 (Appleby), applied to a fold of the two halves.
+__device__ __forceinline__ unsigned long long mix128(u128 k) {
+  unsigned long long h = k.lo ^ (k.hi * 0x9E3779B97F4A7C15ull) ^ (k.hi >> 29);
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
+  return h;
+}
+
+__device__ __forceinline__ uint32_t table_mask(uint32_t log2S) {
+  return (log2S >= 32) ? 0xFFFFFFFFu : ((1u << log2S) - 1u);
+}
+
+// Exact inserts into an open-addressing table of 2^log2S 16-byte slots, for
+// the VEC keys of one thread at once (their probes stay in flight together).
+//
+// A slot is current when its top `ebits` bits equal `epoch` (1..2^ebits-1);
+// any other value (zero, or a key of an earlier pass) counts as free, so the
+// table needs no clearing between passes.  Within a pass a slot changes at
+// most once (free -> key).  That makes the weak first probe safe: a stale value
+// only sends the thread to the CAS, which is atomic at L2, and a current value
+// is final.  Linear probing; the table is sized to at least twice the number of
+// distinct keys a pass can hold, so probe sequences are short.
+//   want[v]  : insert key[v]
+//   slot[v]  : in = home slot, out = the key's slot (its new label)
+//   is_new[v]: this call created the entry
+template <int VEC>
+__device__ __forceinline__ void table_insert_vec(u128 *table, uint32_t mask, const u128 (&key)[VEC], uint32_t ebits,
+                                                 uint32_t epoch, const bool (&want)[VEC], uint32_t (&slot)[VEC],
+                                                 bool (&is_new)[VEC], uint32_t *err) {
+  const uint32_t eshift = 64u - ebits;
+  bool pending[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    pending[v] = want[v];
+    is_new[v] = false;
+  }
+  for (uint64_t iter = 0; iter <= (uint64_t)mask + 1; ++iter) {
+    bool any = false;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) any |= pending[v];
+    if (!any) return;
+    u128 cur[VEC], old[VEC];
+    bool cas[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v)
+      if (pending[v]) cur[v] = ld_b128_weak(table + slot[v]);
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      cas[v] = false;
+      if (!pending[v]) continue;
+      if ((uint32_t)(cur[v].hi >> eshift) == epoch) {
+        if (eq128(cur[v], key[v])) pending[v] = false;   // found
+        else slot[v] = (slot[v] + 1u) & mask;             // owned by another key
+      } else {
+        old[v] = cas_b128(table + slot[v], cur[v], key[v]);
+        cas[v] = true;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      if (!cas[v]) continue;
+      if (eq128(old[v], cur[v])) {               // we wrote the key
+        pending[v] = false;
+        is_new[v] = true;
+      } else if ((uint32_t)(old[v].hi >> eshift) == epoch) {
+        if (eq128(old[v], key[v])) pending[v] = false;   // someone else wrote our key
+        else slot[v] = (slot[v] + 1u) & mask;
+      }
+      // else: the slot held another stale value; retry it with that value
+    }
+  }
+  atomicOr(err, ERR_TABLE_FULL);
+}
+
+// Per-block cache of (key -> slot) for the current pass, in shared memory.  A
+// key that many states share (a large block that does not split) then reaches
+// the global table once per thread block instead of once per warp.  Entries
+// are claimed with a 32-bit tag; the claiming thread publishes the key and its
+// slot before it waits on any other entry, so waits always end.
+struct CtaCache {
+  static constexpr uint32_t M = 256;
+  uint32_t tag[M];
+  uint32_t ready[M];
+  uint32_t slot[M];
+  u128 key[M];
+};
+
+__device__ __forceinline__ void cta_cache_clear(CtaCache *c) {
+  for (uint32_t i = threadIdx.x; i < CtaCache::M; i += blockDim.x) {
+    c->tag[i] = 0u;
+    c->ready[i] = 0u;
+  }
+  __syncthreads();
+}
+
+// Warp-cooperative exact insert: lanes whose keys (for the same v) are equal
+// send one insert and share its slot.  Grouping uses a 32-bit hash; a lane
+// adopts its group leader's slot only after comparing the full 128-bit key, so
+// a hash collision just costs that lane its own insert.  The group leader then
+// consults the block's cache, and only misses reach the global table.  All 32
+// lanes must call this; lanes with valid = false neither insert nor count.
+template <int VEC>
+__device__ __forceinline__ void warp_insert(u128 *table, uint32_t log2S, const u128 (&key)[VEC], bool valid,
+                                            uint32_t ebits, uint32_t epoch, uint32_t (&label)[VEC],
+                                            uint32_t &created, uint32_t *err, CtaCache *cache) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t mask = table_mask(log2S);
+  const unsigned vmask = __ballot_sync(0xFFFFFFFFu, valid);
+  uint32_t slot[VEC], leader[VEC], ci[VEC], tg[VEC];
+  bool want[VEC], is_new[VEC], claimed[VEC], waiter[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    const unsigned long long h = mix128(key[v]);
+    slot[v] = (uint32_t)(h >> 32) & mask;
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, (uint32_t)h) & vmask;
+    uint32_t ld = valid ? (uint32_t)(__ffs(grp) - 1) : lane;
+    const unsigned long long llo = __shfl_sync(0xFFFFFFFFu, key[v].lo, ld);
+    const unsigned long long lhi = __shfl_sync(0xFFFFFFFFu, key[v].hi, ld);
+    if (llo != key[v].lo || lhi != key[v].hi) ld = lane;   // same hash, different key
+    leader[v] = ld;
+    want[v] = valid && ld == lane;
+    tg[v] = (uint32_t)h | 1u;
+    ci[v] = ((uint32_t)h >> 8) % CtaCache::M;
+    claimed[v] = waiter[v] = false;
+  }
+  // 1. claim cache entries (or find them claimed by another warp of the block)
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    if (!want[v]) continue;
+    const uint32_t old = atomicCAS(&cache->tag[ci[v]], 0u, tg[v]);
+    if (old == 0u) {
+      claimed[v] = true;
+      cache->key[ci[v]] = key[v];
+    } else if (old == tg[v]) {
+      waiter[v] = true;
+      want[v] = false;   // resolved through the cache below, if the key matches
+    }
+  }
+  // 2. global inserts for claimed entries and cache misses, then publish
+  table_insert_vec<VEC>(table, mask, key, ebits, epoch, want, slot, is_new, err);
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    if (!claimed[v]) continue;
+    cache->slot[ci[v]] = slot[v];
+    __threadfence_block();
+    atomicExch(&cache->ready[ci[v]], 1u);
+  }
+  // 3. entries claimed by other threads: wait (bounded), compare the full key
+  bool retry[VEC];
+  bool any_retry = false;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    retry[v] = false;
+    if (!waiter[v]) continue;
+    uint32_t spins = 0;
+    while (atomicAdd(&cache->ready[ci[v]], 0u) == 0u && ++spins < (1u << 22)) {
+    }
+    __threadfence_block();
+    const u128 ck = cache->key[ci[v]];
+    if (spins < (1u << 22) && eq128(ck, key[v])) {
+      slot[v] = cache->slot[ci[v]];
+    } else {
+      retry[v] = true;
+      any_retry = true;
+    }
+  }
+  if (any_retry) {
+    bool is_new2[VEC];
+    table_insert_vec<VEC>(table, mask, key, ebits, epoch, retry, slot, is_new2, err);
+#pragma unroll
+    for (int v = 0; v < VEC; ++v)
+      if (retry[v] && is_new2[v]) is_new[v] = true;
+  }
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    label[v] = __shfl_sync(0xFFFFFFFFu, slot[v], leader[v]);
+    if (is_new[v]) ++created;
+  }
+}
+
+// ----------------------------------------------------------------- reductions / scans
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (uint32_t o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the prefix and
+// writes the block total to *total.  `smem` holds blockDim.x/32 words.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *smem, uint32_t *total) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t incl = warp_incl_scan(v);
+  if (lane == 31) smem[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = (lane < nw) ? smem[lane] : 0u;
+    w = warp_incl_scan(w);
+    if (lane < nw) smem[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t warp_prefix = (warp == 0) ? 0u : smem[warp - 1];
+  *total = smem[nw - 1];
+  __syncthreads();
+  return warp_prefix + incl - v;
+}
+
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t *smem) {
+  uint32_t total;
+  (void)block_excl_scan(v, smem, &total);
+  return total;
+}
+
+}  // namespace dfa

@@ -1,0 +1,216 @@
+"""GPU parity: signature refinement (Moore / sortPR semantics) and equivalence
+through the C ABI, element by element against the CPU oracle.
+
+All partitions are compared bit for bit in canonical numbering; round counts
+must match exactly.  Integer work: the tolerance is zero.
+"""
+import numpy as np
+import pytest
+
+import dfagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2508_20735_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def _dev(A):
+    import torch
+    return (torch.from_numpy(np.ascontiguousarray(A.delta).view(np.int32)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(A.accept)).cuda())
+
+
+def _gpu_moore(g, A, **kw):
+    d, a = _dev(A)
+    block, res = g.minimise(d, a, **kw)
+    return block.cpu().numpy().view(np.uint32), res
+
+
+def _assert_parity(g, A, ref=None, **kw):
+    ref = ref or oracle.moore(A.delta, A.accept)
+    got, res = _gpu_moore(g, A, **kw)
+    assert np.array_equal(got, ref.block)
+    assert res.num_blocks == ref.num_blocks
+    assert (res.rounds_changed, res.rounds_executed) == (ref.rounds_changed, ref.rounds_executed), ref.counts
+    return res
+
+
+def test_config1_random_n10000_k2(g):
+    A = dfagen.random_dfa(10_000, 2, 0.5, 1)
+    _assert_parity(g, A)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 63, 64, 65, 511, 512, 513, 1000, 4097, 65_537, 100_003, 262_144])
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 5])
+def test_random_sizes_ragged(g, n, k):
+    A = dfagen.random_dfa(n, k, 0.5, 1000 + n + k)
+    _assert_parity(g, A)
+
+
+@pytest.mark.parametrize("schedule", [1, 2, 4])
+@pytest.mark.parametrize("n,k", [(4096, 2), (100_000, 4), (30_001, 3)])
+def test_vector_widths(g, schedule, n, k):
+    """Every kernel width (states per thread) gives the same result."""
+    A = dfagen.random_dfa(n, k, 0.5, 31 + n)
+    _assert_parity(g, A, schedule=schedule)
+
+
+@pytest.mark.parametrize("p", [0.0, 1.0, 0.01, 0.3, 0.9])
+def test_acceptance_extremes(g, p):
+    A = dfagen.random_dfa(5000, 3, p, 7)
+    _assert_parity(g, A)
+
+
+@pytest.mark.parametrize("n,k", [(10_000, 8), (20_000, 12), (3000, 40), (777, 100)])
+def test_multi_stage_keys(g, n, k):
+    """Signatures wider than one 128-bit key are renumbered in several exact stages."""
+    A = dfagen.random_dfa(n, k, 0.5, n + k)
+    _assert_parity(g, A)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_planted_redundancy(g, seed):
+    """Real merges: the expected partition is 'copies of the same state'."""
+    base = dfagen.random_dfa(3000, 3 + seed % 3, 0.5, seed + 40)
+    assert oracle.hopcroft(base.delta, base.accept).max() + 1 == base.n     # the base is minimal
+    P, origin = dfagen.planted_redundancy(base, 6, seed)
+    ref = oracle.moore(P.delta, P.accept)
+    assert np.array_equal(ref.block, oracle.canonical(origin))
+    _assert_parity(g, P, ref)
+
+
+def test_few_targets_heavy_merging(g):
+    """Targets restricted to a few states: most states are equivalent, blocks are huge."""
+    n, k = 200_000, 3
+    d = dfagen.bounded(9, 91, n * k, 5).reshape(k, n)
+    acc = dfagen.bernoulli(9, 92, n, 0.5)
+    _assert_parity(g, dfagen.DFA(d, acc, 0))
+
+
+@pytest.mark.parametrize("i", [8, 12, 16])
+def test_fibonacci(g, i):
+    A = dfagen.fibonacci_dfa(i)
+    res = _assert_parity(g, A)
+    assert res.num_blocks == A.n and res.rounds_executed == A.n - 1
+
+
+@pytest.mark.parametrize("m", [3, 8, 12, 15])
+def test_bit_splitters(g, m):
+    B = dfagen.bit_splitter(m)
+    res = _assert_parity(g, B)
+    assert res.rounds_changed == m - 1
+
+
+def test_chain_deep_rounds(g):
+    C = dfagen.chain_dfa(1 << 12)
+    res = _assert_parity(g, C)
+    assert res.rounds_changed == (1 << 12) - 2
+
+
+def test_cycle(g):
+    C = dfagen.cycle_dfa(14)
+    _assert_parity(g, C)
+
+
+def test_host_buffers_e2e(g):
+    """Host (numpy) inputs and output go through the same call: staged copies."""
+    A = dfagen.random_dfa(50_000, 3, 0.5, 17)
+    ref = oracle.moore(A.delta, A.accept)
+    block, res = g.minimise(A.delta, A.accept)
+    assert isinstance(block, np.ndarray)
+    assert np.array_equal(block, ref.block)
+    assert res.rounds_executed == ref.rounds_executed
+
+
+def test_deterministic(g):
+    A = dfagen.random_dfa(300_000, 4, 0.5, 3)
+    a, r1 = _gpu_moore(g, A)
+    b, r2 = _gpu_moore(g, A)
+    assert np.array_equal(a, b) and r1.rounds_executed == r2.rounds_executed
+
+
+def test_large_random_2p22(g):
+    """A quarter of the 2^24-state workload, compared in full with the oracle."""
+    A = dfagen.random_dfa(1 << 22, 4, 0.5, 2)
+    _assert_parity(g, A)
+
+
+# ---------------------------------------------------------------- errors
+
+def test_bad_transition_target(g):
+    A = dfagen.random_dfa(1000, 2, 0.5, 5)
+    A.delta[1][123] = 1000
+    with pytest.raises(g.DfaError) as e:
+        _gpu_moore(g, A)
+    assert e.value.status == g.DFA_EINVAL
+
+
+def test_workspace_too_small(g):
+    import torch
+    A = dfagen.random_dfa(1000, 2, 0.5, 5)
+    d, a = _dev(A)
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(g.DfaError) as e:
+        g.minimise(d, a, workspace=ws)
+    assert e.value.status == g.DFA_EINVAL and "workspace too small" in str(e.value)
+
+
+def test_max_rounds(g):
+    C = dfagen.chain_dfa(256)
+    d, a = _dev(C)
+    block, res = g.minimise(d, a, max_rounds=5, check=False)
+    assert res.call_status == g.DFA_EMAXROUNDS and res.rounds_executed == 5
+    ref = oracle.moore(C.delta, C.accept, max_rounds=5)
+    assert np.array_equal(block.cpu().numpy().view(np.uint32), oracle.canonical(ref.block))
+
+
+def test_timeout_returns_status_and_context_survives(g):
+    """A call-time limit far below the work needed ends the launch with
+    DFA_ETIMEOUT (device-side, no fault); the next call on the context works."""
+    C = dfagen.chain_dfa(1 << 16)             # 65,535 rounds
+    d, a = _dev(C)
+    _, res = g.minimise(d, a, timeout_ns=2_000_000, check=False)   # 2 ms
+    assert res.call_status == g.DFA_ETIMEOUT
+    A = dfagen.random_dfa(4096, 2, 0.5, 1)
+    _assert_parity(g, A)
+
+
+# ---------------------------------------------------------------- equivalence
+
+@pytest.mark.parametrize("req", range(12))
+def test_equivalence_pairs(g, req):
+    A, B, expect = dfagen.equivalence_pair(req, 5, n_lo=1000, n_hi=60_000)
+    eq, res = g.equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start))
+    assert eq == expect
+    ref = oracle.equivalent(A.delta, A.accept, A.start, B.delta, B.accept, B.start)
+    assert eq == ref.equivalent
+    assert (res.num_blocks, res.rounds_executed) == (ref.refine.num_blocks, ref.refine.rounds_executed)
+    eq2, res2 = g.equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start), early_exit=True)
+    assert eq2 == expect
+    if not expect:
+        cex = oracle.shortest_cex(A.delta, A.accept, A.start, B.delta, B.accept, B.start)
+        assert res2.rounds_executed == cex
+
+
+def test_equivalence_start_acceptance_differs(g):
+    C = dfagen.cycle_dfa(7)
+    s2 = int(np.nonzero(C.accept)[0][0])
+    eq, res = g.equivalent((C.delta, C.accept, 0), (C.delta, C.accept, s2), early_exit=True)
+    assert not eq and res.rounds_executed == 0
+    eq, res = g.equivalent((C.delta, C.accept, 0), (C.delta, C.accept, s2))
+    assert not eq
+
+
+def test_equivalence_self(g):
+    A = dfagen.random_dfa(12_345, 2, 0.5, 8)
+    eq, _ = g.equivalent((A.delta, A.accept, 3), (A.delta, A.accept, 3))
+    assert eq
