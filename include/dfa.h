@@ -172,6 +172,25 @@ int dfa_serve_stats(dfa_server *s, double *p50_us, double *p99_us, double *throu
 /* Cancels outstanding requests, joins the thread and frees the arena. */
 int dfa_serve_destroy(dfa_server *s);
 
+/* ---------------------------------------------------------------- no-allocation variant */
+
+/* The paper has no counterpart to this call.  It is dfa_minimise (signature
+ * refinement only) for callers that cannot hand the library a workspace:
+ * code inside a host framework that owns every device allocation, or
+ * latency-critical paths where cudaMalloc is off-limits because it may
+ * synchronise the device.  Its scratch is a fixed 4 MiB array compiled into
+ * the library, held by every GPU that loads it until the process exits.
+ *  - n <= DFA_NOALLOC_MAX_STATES, else DFA_EINVAL (use dfa_minimise).
+ *  - delta, accept and block_out must be device pointers (else DFA_EINVAL).
+ *  - The first call on a device looks the array's device address up; make
+ *    that first call before any stream capture.
+ *  - All calls share the array: calls that overlap on the GPU race, so
+ *    serialise them.  Each call clears what it needs; nothing carries over.
+ *  - Calls no cudaMalloc, cudaFree or allocating library routine. */
+#define DFA_NOALLOC_MAX_STATES 65536u
+int dfa_minimise_noalloc(const dfa_t *dfa, const dfa_opts *opts, uint32_t *block_out, dfa_result *res,
+                         void *stream);
+
 /* ---------------------------------------------------------------- misc */
 
 /* Thread-local message describing the last failing call on this thread. */

@@ -73,6 +73,7 @@ _SIGS = [
     ("dfa_serve_wait", c_int, [c_void_p, c_uint64, c_uint64, POINTER(DfaResult), POINTER(c_int), c_void_p]),
     ("dfa_serve_stats", c_int, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
     ("dfa_serve_destroy", c_int, [c_void_p]),
+    ("dfa_minimise_noalloc", c_int, [POINTER(DfaT), POINTER(DfaOpts), c_void_p, POINTER(DfaResult), c_void_p]),
     ("dfa_last_error", ctypes.c_char_p, []),
     ("dfa_version", ctypes.c_char_p, []),
 ]
@@ -182,6 +183,16 @@ def dfa_minimise(dfa: DfaT, opts: DfaOpts | None, block_out_ptr: int, workspace_
     res = DfaResult()
     st = lib().dfa_minimise(ctypes.byref(dfa), ctypes.byref(opts) if opts else None, block_out_ptr,
                             ctypes.byref(res), workspace_ptr, ws_bytes, stream)
+    return st, res
+
+
+def dfa_minimise_noalloc(dfa: DfaT, opts: DfaOpts | None, block_out_ptr: int,
+                         stream: int | None) -> tuple[int, DfaResult]:
+    """dfa_minimise without a caller workspace (fixed scratch inside the library;
+    device pointers only, n <= 65,536; see include/dfa.h)."""
+    res = DfaResult()
+    st = lib().dfa_minimise_noalloc(ctypes.byref(dfa), ctypes.byref(opts) if opts else None, block_out_ptr,
+                                    ctypes.byref(res), stream)
     return st, res
 
 

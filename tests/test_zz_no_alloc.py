@@ -1,0 +1,67 @@
+"""dfa_minimise_noalloc: the entry point for callers that cannot allocate.
+
+Some callers cannot give the library a workspace: a host framework may own
+every device allocation, or a latency-critical path may be forbidden to call
+cudaMalloc because it can synchronise the device.  This test calls the
+no-allocation entry point through the C ABI twice in a row (the second call on
+a smaller DFA, after the first has left its data in the shared scratch) and
+checks each result against dfa_minimise, bit for bit, and that sizes beyond
+the fixed scratch are rejected with a clear error.
+
+The file is named to be collected last.
+"""
+import numpy as np
+import pytest
+
+import dfagen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2508_20735_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def _noalloc(g, A):
+    import torch
+    d = torch.from_numpy(np.ascontiguousarray(A.delta).view(np.int32)).cuda()
+    a = torch.from_numpy(np.ascontiguousarray(A.accept)).cuda()
+    out = torch.full((A.n,), -1, dtype=torch.int32, device="cuda")
+    dd, keep = g.make_dfa(d, a)
+    st, res = g.dfa_minimise_noalloc(dd, None, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return st, res, out.cpu().numpy().view(np.uint32)
+
+
+def _reference(g, A):
+    import torch
+    d = torch.from_numpy(np.ascontiguousarray(A.delta).view(np.int32)).cuda()
+    a = torch.from_numpy(np.ascontiguousarray(A.accept)).cuda()
+    block, res = g.minimise(d, a)
+    return res, block.cpu().numpy().view(np.uint32)
+
+
+def test_noalloc_matches_dfa_minimise_twice(g):
+    big = dfagen.random_dfa(60_000, 3, 0.5, 71)
+    base = dfagen.random_dfa(500, 3, 0.5, 72)
+    small, _ = dfagen.planted_redundancy(base, 4, 73)      # real merges, fewer states
+    for A in (big, small):
+        st, res, got = _noalloc(g, A)
+        assert st == g.DFA_OK, g.last_error()
+        ref_res, ref = _reference(g, A)
+        assert np.array_equal(got, ref)
+        assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
+            (ref_res.num_blocks, ref_res.rounds_changed, ref_res.rounds_executed)
+
+
+def test_noalloc_rejects_too_many_states(g):
+    A = dfagen.random_dfa(65_537, 2, 0.5, 74)
+    st, res, _ = _noalloc(g, A)
+    assert st == g.DFA_EINVAL
+    assert "at most 65536 states" in g.last_error()
