@@ -187,73 +187,6 @@ __device__ __forceinline__ void clear_table(u128 *table, uint32_t log2S) {
   }
 }
 
-// Canonical numbering of the final labels: block id = rank of its smallest
-// state.  `B` is the number of blocks.  Returns false if a barrier failed.
-__device__ bool canonicalise(const MooreArgs &A, const uint32_t *__restrict__ lab, uint32_t B, uint32_t *s_red) {
-  Ctrl *C = A.ctrl;
-  const uint32_t n = A.n;
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  if (B == n) {   // every block is a singleton {q}: its number is q
-    for (uint32_t q = tid; q < n; q += stride) A.out[q] = q;
-    if (blockIdx.x == 0 && threadIdx.x == 0) C->num_blocks = n;
-    return true;
-  }
-  const size_t S = (size_t)1 << A.log2S;
-  for (size_t i = tid; i < S; i += stride) A.minrep[i] = 0xFFFFFFFFu;
-  if (!grid_sync(C, A.barrier_ns)) return false;
-  {
-    // lanes hold consecutive states, so the lowest lane of a label group holds
-    // the group's smallest state: one atomic per (warp, label)
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t gwarp = tid >> 5, nwarps = stride >> 5;
-    for (uint64_t base = (uint64_t)gwarp * 32; base < n; base += (uint64_t)nwarps * 32) {
-      const uint32_t q = (uint32_t)base + lane;
-      const bool valid = q < n;
-      const uint32_t l = valid ? lab[q] : 0u;
-      const unsigned grp = __match_any_sync(0xFFFFFFFFu, l) & __ballot_sync(0xFFFFFFFFu, valid);
-      if (valid && lane == (uint32_t)(__ffs(grp) - 1)) atomicMin(&A.minrep[l], q);
-    }
-  }
-  if (!grid_sync(C, A.barrier_ns)) return false;
-  // contiguous chunk per block, a multiple of blockDim
-  uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  chunk = (chunk + blockDim.x - 1) / blockDim.x * blockDim.x;
-  const uint64_t beg64 = (uint64_t)blockIdx.x * chunk;
-  const uint32_t beg = beg64 < n ? (uint32_t)beg64 : n;
-  const uint32_t end = (uint64_t)beg + chunk < n ? beg + chunk : n;
-  uint32_t cnt = 0;
-  for (uint32_t q = beg + threadIdx.x; q < end; q += blockDim.x) {
-    const uint8_t f = A.minrep[lab[q]] == q;
-    A.flag[q] = f;
-    cnt += f;
-  }
-  const uint32_t bsum = block_sum(cnt, s_red);
-  if (threadIdx.x == 0) A.partials[blockIdx.x] = bsum;
-  if (!grid_sync(C, A.barrier_ns)) return false;
-  // offset of this block = sum of earlier blocks' counts; total = all
-  uint32_t pre = 0, tot = 0;
-  for (uint32_t b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-    const uint32_t v = A.partials[b];
-    tot += v;
-    if (b < blockIdx.x) pre += v;
-  }
-  pre = block_sum(pre, s_red);
-  tot = block_sum(tot, s_red);
-  uint32_t run = pre;
-  for (uint32_t base = beg; base < end; base += blockDim.x) {
-    const uint32_t q = base + threadIdx.x;
-    const uint32_t f = (q < end) ? A.flag[q] : 0u;
-    uint32_t tile_total;
-    const uint32_t r = block_excl_scan(f, s_red, &tile_total);
-    if (f) A.minrep[lab[q]] = run + r;
-    run += tile_total;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) C->num_blocks = tot;
-  if (!grid_sync(C, A.barrier_ns)) return false;
-  for (uint32_t q = tid; q < n; q += stride) A.out[q] = A.minrep[lab[q]];
-  return true;
-}
-
 template <int VEC>
 __global__ void __launch_bounds__(kThreads) moore_kernel(MooreArgs A) {
   __shared__ uint32_t s_red[kThreads / 32];
@@ -343,7 +276,9 @@ __global__ void __launch_bounds__(kThreads) moore_kernel(MooreArgs A) {
       C->rounds_executed = r;
       C->rounds_changed = changed;
     }
-    ok = canonicalise(A, A.lab[final_buf], B_final, s_red);
+    ok = canonicalise(CanonArgs{A.n, A.lab[final_buf], (size_t)1 << A.log2S, A.minrep, A.flag, A.partials, A.out,
+                                A.ctrl, A.barrier_ns},
+                      B_final, s_red);
   }
   if (leader) C->t_end = gtimer();
 }
