@@ -284,6 +284,7 @@ struct CtaCache {
   uint32_t tag[M];
   uint32_t ready[M];
   uint32_t slot[M];
+  uint32_t ns[M];          // key namespace (the DFA of a batch whose table the slot belongs to)
   u128 key[M];
 };
 
@@ -301,10 +302,12 @@ __device__ __forceinline__ void cta_cache_clear(CtaCache *c) {
 // a hash collision just costs that lane its own insert.  The group leader then
 // consults the block's cache, and only misses reach the global table.  All 32
 // lanes must call this; lanes with valid = false neither insert nor count.
+// `ns` names the table the keys belong to (warps of one block may serve
+// different tables); a cached slot is reused only for the same key and ns.
 template <int VEC>
 __device__ __forceinline__ void warp_insert(u128 *table, uint32_t log2S, const u128 (&key)[VEC], bool valid,
                                             uint32_t ebits, uint32_t epoch, uint32_t (&label)[VEC],
-                                            uint32_t &created, uint32_t *err, CtaCache *cache) {
+                                            uint32_t &created, uint32_t *err, CtaCache *cache, uint32_t ns = 0) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t mask = table_mask(log2S);
   const unsigned vmask = __ballot_sync(0xFFFFFFFFu, valid);
@@ -321,8 +324,9 @@ __device__ __forceinline__ void warp_insert(u128 *table, uint32_t log2S, const u
     if (llo != key[v].lo || lhi != key[v].hi) ld = lane;   // same hash, different key
     leader[v] = ld;
     want[v] = valid && ld == lane;
-    tg[v] = (uint32_t)h | 1u;
-    ci[v] = ((uint32_t)h >> 8) % CtaCache::M;
+    const uint32_t hn = (uint32_t)h ^ (ns * 0x9E3779B9u);
+    tg[v] = hn | 1u;
+    ci[v] = (hn >> 8) % CtaCache::M;
     claimed[v] = waiter[v] = false;
   }
   // 1. claim cache entries (or find them claimed by another warp of the block)
@@ -333,6 +337,7 @@ __device__ __forceinline__ void warp_insert(u128 *table, uint32_t log2S, const u
     if (old == 0u) {
       claimed[v] = true;
       cache->key[ci[v]] = key[v];
+      cache->ns[ci[v]] = ns;
     } else if (old == tg[v]) {
       waiter[v] = true;
       want[v] = false;   // resolved through the cache below, if the key matches
@@ -359,7 +364,7 @@ __device__ __forceinline__ void warp_insert(u128 *table, uint32_t log2S, const u
     }
     __threadfence_block();
     const u128 ck = cache->key[ci[v]];
-    if (spins < (1u << 22) && eq128(ck, key[v])) {
+    if (spins < (1u << 22) && eq128(ck, key[v]) && cache->ns[ci[v]] == ns) {
       slot[v] = cache->slot[ci[v]];
     } else {
       retry[v] = true;

@@ -1,20 +1,9 @@
-// Batched minimisation and the serving loop.
+// The serving loop.
 #include "api_util.h"
 
 using namespace dfa;
 
 extern "C" {
-
-size_t dfa_batch_workspace_size(const dfa_t *dfas, uint32_t count, const dfa_opts *opts) {
-  (void)dfas; (void)count; (void)opts;
-  return 0;
-}
-
-int dfa_minimise_batch(const dfa_t *dfas, uint32_t count, const dfa_opts *opts, uint32_t *block_out,
-                       dfa_result *res, void *workspace, size_t ws_bytes, void *stream) {
-  (void)dfas; (void)count; (void)opts; (void)block_out; (void)res; (void)workspace; (void)ws_bytes; (void)stream;
-  return fail(DFA_EINVAL, "batch path not built yet");
-}
 
 int dfa_serve_create(dfa_server **out, size_t hbm_budget_bytes, uint32_t max_slots, int device) {
   (void)out; (void)hbm_budget_bytes; (void)max_slots; (void)device;

@@ -1,0 +1,113 @@
+"""GPU parity: dfa_minimise_batch.  Each DFA's partition (numbered within the
+DFA) and round counts must equal the oracle's and dfa_minimise's on that DFA
+alone, under every schedule and under the autotuner."""
+import os
+
+import numpy as np
+import pytest
+
+import dfagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g(tmp_path_factory):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    os.environ["DFA_AUTOTUNE_CACHE"] = str(tmp_path_factory.mktemp("tune") / "autotune.json")
+    import paper_2508_20735_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def _dev(A):
+    import torch
+    return (torch.from_numpy(np.ascontiguousarray(A.delta).view(np.int32)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(A.accept)).cuda())
+
+
+def _batch(g, dfas, schedule=-1, host=False, **kw):
+    items = [(A.delta, A.accept) if host else _dev(A) for A in dfas]
+    out, res = g.minimise_batch(items, schedule=schedule, **kw)
+    blocks = out.cpu().numpy().view(np.uint32)
+    offs = np.concatenate([[0], np.cumsum([A.n for A in dfas])])
+    return [blocks[offs[i]:offs[i + 1]] for i in range(len(dfas))], res
+
+
+def _mixed():
+    dfas = [dfagen.random_dfa(n, k, p, 900 + i) for i, (n, k, p) in enumerate(
+        [(1, 2, 0.5), (2, 1, 0.5), (3, 0, 0.5), (5, 3, 0.5), (64, 2, 0.3), (257, 4, 0.3), (1000, 8, 0.3),
+         (3000, 40, 0.5), (4096, 2, 0.0), (777, 3, 1.0), (10_000, 5, 0.3)])]
+    dfas.append(dfagen.fibonacci_dfa(11))
+    dfas.append(dfagen.bit_splitter(9))
+    base = dfagen.random_dfa(300, 3, 0.5, 61)
+    dfas.append(dfagen.planted_redundancy(base, 5, 2)[0])
+    dfas.append(dfagen.chain_dfa(300))
+    return dfas
+
+
+@pytest.mark.parametrize("schedule", [0, 1, -1])
+def test_mixed_batch_against_oracle(g, schedule):
+    dfas = _mixed()
+    blocks, res = _batch(g, dfas, schedule=schedule)
+    for A, b, r in zip(dfas, blocks, res):
+        ref = oracle.moore(A.delta, A.accept)
+        assert np.array_equal(b, ref.block)
+        assert (r.num_blocks, r.rounds_changed, r.rounds_executed) == \
+            (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
+
+
+def test_batch_equals_alone_and_host_inputs(g):
+    dfas = _mixed()[:10]
+    blocks, res = _batch(g, dfas, host=True)
+    for A, b, r in zip(dfas, blocks, res):
+        d, a = _dev(A)
+        alone, ra = g.minimise(d, a)
+        assert np.array_equal(b, alone.cpu().numpy().view(np.uint32))
+        assert (r.num_blocks, r.rounds_executed) == (ra.num_blocks, ra.rounds_executed)
+
+
+def test_batch_recipe_sample(g):
+    """256 DFAs of the batch recipe (n log-uniform in [64, 65536], k in 2..8)."""
+    dfas = dfagen.batch_dfas(256, 64, 65_536, 2, 8, 0.3, 4)
+    blocks, res = _batch(g, dfas)
+    for A, b, r in zip(dfas, blocks, res):
+        ref = oracle.moore(A.delta, A.accept)
+        assert np.array_equal(b, ref.block)
+        assert r.rounds_executed == ref.rounds_executed
+
+
+def test_batch_4096_full_size(g):
+    """The full 4,096-DFA workload: every DFA equals its stand-alone refinement
+    (GPU), a sample of 64 equals the oracle."""
+    dfas = dfagen.batch_dfas(4096, 64, 65_536, 2, 8, 0.3, 4)
+    blocks, res = _batch(g, dfas)
+    rng = np.random.default_rng(0)
+    sample = set(rng.choice(len(dfas), 64, replace=False).tolist())
+    for i, (A, b, r) in enumerate(zip(dfas, blocks, res)):
+        d, a = _dev(A)
+        alone, ra = g.minimise(d, a)
+        assert np.array_equal(b, alone.cpu().numpy().view(np.uint32)), i
+        assert (r.num_blocks, r.rounds_executed) == (ra.num_blocks, ra.rounds_executed), i
+        if i in sample:
+            ref = oracle.moore(A.delta, A.accept)
+            assert np.array_equal(b, ref.block), i
+
+
+def test_batch_max_rounds(g):
+    dfas = [dfagen.chain_dfa(50), dfagen.random_dfa(100, 2, 0.5, 3)]
+    blocks, res = _batch(g, dfas, max_rounds=3, check=False)
+    assert res[0].status == g.DFA_EMAXROUNDS and res[0].rounds_executed == 3
+    ref = oracle.moore(dfas[0].delta, dfas[0].accept, max_rounds=3)
+    assert np.array_equal(blocks[0], ref.block)
+
+
+def test_batch_bad_delta(g):
+    A = dfagen.random_dfa(100, 2, 0.5, 3)
+    B = dfagen.random_dfa(50, 2, 0.5, 4)
+    B.delta[1][7] = 50
+    with pytest.raises(g.DfaError):
+        _batch(g, [A, B])
