@@ -158,8 +158,10 @@ int dfa_serve_submit(dfa_server *s, int kind, const dfa_t *a, const dfa_t *b, co
 
 /* DFA_EBUSY while the request is queued or running; DFA_OK (or the request's
  * error) once finished, filling res, *equivalent (equivalence requests) and,
- * if block_out is non-NULL, the partition (host memory, n or n_A + n_B
- * entries).  A finished ticket is released by the first successful poll/wait. */
+ * for a minimisation request with block_out non-NULL, its partition (host
+ * memory, n entries, canonical numbering).  Results equal those of
+ * dfa_minimise / dfa_equivalent on the same input.  A finished ticket is
+ * released by the first poll/wait that returns it. */
 int dfa_serve_poll(dfa_server *s, uint64_t ticket, dfa_result *res, int *equivalent, uint32_t *block_out);
 
 /* As dfa_serve_poll, but blocks up to timeout_ns (0 = forever). */
@@ -169,7 +171,8 @@ int dfa_serve_wait(dfa_server *s, uint64_t ticket, uint64_t timeout_ns, dfa_resu
 /* Latency percentiles (submit to completion) and throughput of finished requests. */
 int dfa_serve_stats(dfa_server *s, double *p50_us, double *p99_us, double *throughput_rps);
 
-/* Cancels outstanding requests, joins the thread and frees the arena. */
+/* Cancels outstanding requests, joins the thread and frees the arena.  No other
+ * call on `s` may run concurrently with or after this one. */
 int dfa_serve_destroy(dfa_server *s);
 
 /* ---------------------------------------------------------------- no-allocation variant */

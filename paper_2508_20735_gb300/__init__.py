@@ -302,3 +302,77 @@ def header_functions() -> list[str]:
     src = open(path).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(dfa_[a-z_0-9]+)\s*\(", src)))
+
+
+class Server:
+    """Thin wrapper over dfa_serve_*: continuous batching of minimisation and
+    equivalence requests on one device arena of `hbm_budget_bytes`."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 64, device: int = 0):
+        h = c_void_p()
+        st = lib().dfa_serve_create(ctypes.byref(h), int(hbm_budget_bytes), int(max_slots), int(device))
+        if st != DFA_OK:
+            raise DfaError(st, last_error())
+        self._h = h
+
+    def submit_minimise(self, delta, accept, max_rounds=0) -> int:
+        d, keep = make_dfa(delta, accept)
+        t = c_uint64()
+        o = make_opts("moore", max_rounds)
+        st = lib().dfa_serve_submit(self._h, DFA_REQ_MINIMISE, ctypes.byref(d), None, ctypes.byref(o),
+                                    ctypes.byref(t))
+        if st != DFA_OK:
+            raise DfaError(st, last_error())
+        return t.value
+
+    def submit_equivalent(self, A, B, early_exit=False) -> int:
+        a, ka = make_dfa(A[0], A[1], A[2])
+        b, kb = make_dfa(B[0], B[1], B[2])
+        t = c_uint64()
+        o = make_opts("moore", flags=DFA_FLAG_EARLY_EXIT if early_exit else 0)
+        st = lib().dfa_serve_submit(self._h, DFA_REQ_EQUIVALENT, ctypes.byref(a), ctypes.byref(b), ctypes.byref(o),
+                                    ctypes.byref(t))
+        if st != DFA_OK:
+            raise DfaError(st, last_error())
+        return t.value
+
+    def poll(self, ticket: int, n: int = 0):
+        """(status, DfaResult, equivalent, blocks-or-None); status DFA_EBUSY while running."""
+        res = DfaResult()
+        eq = c_int(-1)
+        out = np.empty(n, dtype=np.uint32) if n else None
+        st = lib().dfa_serve_poll(self._h, ticket, ctypes.byref(res), ctypes.byref(eq),
+                                  out.ctypes.data if out is not None else None)
+        return st, res, eq.value, out
+
+    def wait(self, ticket: int, n: int = 0, timeout_ns: int = 0):
+        res = DfaResult()
+        eq = c_int(-1)
+        out = np.empty(n, dtype=np.uint32) if n else None
+        st = lib().dfa_serve_wait(self._h, ticket, int(timeout_ns), ctypes.byref(res), ctypes.byref(eq),
+                                  out.ctypes.data if out is not None else None)
+        return st, res, eq.value, out
+
+    def stats(self):
+        p50, p99, rps = c_double(), c_double(), c_double()
+        st = lib().dfa_serve_stats(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(rps))
+        if st != DFA_OK:
+            raise DfaError(st, last_error())
+        return {"p50_us": p50.value, "p99_us": p99.value, "throughput_rps": rps.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dfa_serve_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

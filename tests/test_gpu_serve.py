@@ -1,0 +1,97 @@
+"""GPU: the serving loop (continuous batching).  Every request's result in a
+mix -- requests submitted while others are being refined, admitted as slots
+and arena space free up -- equals the stand-alone call's and the oracle's."""
+import time
+
+import numpy as np
+import pytest
+
+import dfagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2508_20735_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def _requests():
+    reqs = []
+    for i in range(24):
+        if i % 3 == 0:
+            A = dfagen.random_dfa(200 + 397 * i, 2 + i % 3, 0.5, 300 + i)
+            reqs.append(("min", A))
+        else:
+            A, B, eq = dfagen.equivalence_pair(i, 5, n_lo=500, n_hi=40_000)
+            reqs.append(("eq", (A, B, eq)))
+    base = dfagen.random_dfa(500, 3, 0.5, 71)
+    reqs.append(("min", dfagen.planted_redundancy(base, 4, 3)[0]))
+    reqs.append(("min", dfagen.fibonacci_dfa(12)))
+    reqs.append(("min", dfagen.random_dfa(3000, 40, 0.5, 5)))      # multi-stage keys
+    return reqs
+
+
+@pytest.mark.parametrize("slots,budget_mb", [(64, 2048), (3, 64)])
+def test_mix_equals_alone(g, slots, budget_mb):
+    reqs = _requests()
+    with g.Server(budget_mb << 20, max_slots=slots) as srv:
+        tickets = []
+        for j, (kind, item) in enumerate(reqs):
+            if kind == "min":
+                tickets.append(srv.submit_minimise(item.delta, item.accept))
+            else:
+                A, B, _ = item
+                tickets.append(srv.submit_equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start),
+                                                     early_exit=(j % 2 == 0)))
+            if j % 5 == 4:
+                time.sleep(0.002)          # later requests arrive while earlier ones run
+        for j, ((kind, item), t) in enumerate(zip(reqs, tickets)):
+            if kind == "min":
+                st, res, _, blocks = srv.wait(t, n=item.n)
+                assert st == g.DFA_OK, g.last_error()
+                ref = oracle.moore(item.delta, item.accept)
+                assert np.array_equal(blocks, ref.block)
+                assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
+                    (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
+            else:
+                A, B, expect = item
+                st, res, eq, _ = srv.wait(t)
+                assert st == g.DFA_OK, g.last_error()
+                assert eq == int(expect)
+                alone_eq, alone = g.equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start),
+                                               early_exit=(j % 2 == 0))
+                assert bool(eq) == alone_eq
+                assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
+                    (alone.num_blocks, alone.rounds_changed, alone.rounds_executed)
+        s = srv.stats()
+        assert s["p50_us"] > 0 and s["p99_us"] >= s["p50_us"] and s["throughput_rps"] > 0
+
+
+def test_poll_busy_then_done(g):
+    C = dfagen.chain_dfa(1 << 12)      # thousands of rounds: still running at the first poll
+    with g.Server(256 << 20, max_slots=4) as srv:
+        t = srv.submit_minimise(C.delta, C.accept)
+        st, *_ = srv.poll(t)
+        assert st == g.DFA_EBUSY
+        st, res, _, blocks = srv.wait(t, n=C.n)
+        assert st == g.DFA_OK and res.rounds_changed == C.n - 2
+        assert np.array_equal(blocks, np.arange(C.n, dtype=np.uint32))
+
+
+def test_request_beyond_budget_and_destroy_with_pending(g):
+    big = dfagen.random_dfa(1 << 20, 4, 0.5, 1)
+    srv = g.Server(16 << 20, max_slots=2)
+    with pytest.raises(g.DfaError) as e:
+        srv.submit_minimise(big.delta, big.accept)
+    assert e.value.status == g.DFA_ENOMEM
+    for i in range(6):
+        A = dfagen.random_dfa(20_000, 2, 0.5, i)
+        srv.submit_minimise(A.delta, A.accept)
+    srv.close()        # cancels what is still queued; must not hang
