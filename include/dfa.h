@@ -76,6 +76,9 @@ typedef enum dfa_algo {
 
 /* Flags for dfa_opts.flags */
 #define DFA_FLAG_EARLY_EXIT 0x1u   /* equivalence: stop once the start states separate */
+#define DFA_FLAG_TABLE_ONLY 0x2u   /* signature refinement: renumber through the exact hash table in
+                                      every round (no direct or filter rounds); same results, for
+                                      comparisons and tests */
 
 typedef struct dfa_opts {
   int32_t algo;            /* dfa_algo */
@@ -181,7 +184,7 @@ int dfa_serve_destroy(dfa_server *s);
  * refinement only) for callers that cannot hand the library a workspace:
  * code inside a host framework that owns every device allocation, or
  * latency-critical paths where cudaMalloc is off-limits because it may
- * synchronise the device.  Its scratch is a fixed 4 MiB array compiled into
+ * synchronise the device.  Its scratch is a fixed 8 MiB array compiled into
  * the library, held by every GPU that loads it until the process exits.
  *  - n <= DFA_NOALLOC_MAX_STATES, else DFA_EINVAL (use dfa_minimise).
  *  - delta, accept and block_out must be device pointers (else DFA_EINVAL).

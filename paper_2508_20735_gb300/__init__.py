@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "DFA_OK", -1: "DFA_EINVAL", -2: "DFA_ENOMEM", -3: "DFA_ECUDA"
                 -5: "DFA_EMAXROUNDS", -6: "DFA_EBUSY", -7: "DFA_ECANCELLED"}
 ALGOS = {"moore": 0, "naive": 1, "trans": 2}
 DFA_FLAG_EARLY_EXIT = 0x1
+DFA_FLAG_TABLE_ONLY = 0x2
 DFA_REQ_MINIMISE, DFA_REQ_EQUIVALENT = 0, 1
 
 
@@ -227,14 +228,14 @@ def dfa_minimise_batch(dfas, opts: DfaOpts | None, block_out_ptr: int, workspace
 # ----------------------------------------------------------------- conveniences
 
 def minimise(delta, accept, algo="moore", max_rounds=0, timeout_ns=0, out=None, workspace=None, stream=None,
-             check=True, schedule=-1):
+             check=True, schedule=-1, flags=0):
     """Coarsest partition of the DFA given by delta (k, n) and accept (n,).
 
     Arrays may be CUDA tensors, CPU tensors or numpy arrays.  The output has the
     input's kind (CUDA tensor in -> CUDA tensor out; otherwise numpy).
     Returns (block, DfaResult)."""
     d, keep = make_dfa(delta, accept)
-    o = make_opts(algo, max_rounds, timeout_ns, schedule)
+    o = make_opts(algo, max_rounds, timeout_ns, schedule, flags)
     on_dev = _is_cuda(keep[1])
     if out is None:
         if on_dev:

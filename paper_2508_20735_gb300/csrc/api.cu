@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
 
 #include "../../include/dfa.h"
@@ -69,12 +70,34 @@ int check_dfa(const dfa_t *d, const char *name) {
 // ------------------------------------------------------------------ Moore workspace
 static constexpr size_t kMaxGrid = 8192;
 
+// Warps of the Moore kernel's cooperative grid (the largest grid any width
+// uses); without a visible device, the largest grid the launcher accepts.
+static size_t moore_max_warps() {
+  static size_t cached = 0;
+  if (cached) return cached;
+  size_t best = 0;
+  for (uint32_t v : {1u, 2u, 4u}) {
+    LaunchInfo li{};
+    if (moore_grid(v, &li) != cudaSuccess) {
+      cudaGetLastError();
+      return kMaxGrid * 16;
+    }
+    best = std::max(best, (size_t)li.grid * (li.block / 32));
+  }
+  cached = best;
+  return best;
+}
+
 MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_accept, bool stage_out) {
   MooreLayout L{};
   L.log2S = ceil_log2(n * 2 < 64 ? 64 : n * 2);
-  const StagePlan p1 = make_plan(k, 1), pr = make_plan(k, L.log2S);
-  L.plan1 = p1;
-  L.planr = pr;
+  L.mbits = L.log2S + 2 < 31 ? L.log2S + 2 : 31;
+  L.wid = ceil_log2(n) > 0 ? ceil_log2(n) : 1;
+  // every table key (exact-table or filter rounds) has at most
+  // min(125, (k+1)*log2S) bits; the epoch tag takes the rest, at most 32
+  const uint64_t keymax = (uint64_t)(k + 1) * L.log2S < 125 ? (uint64_t)(k + 1) * L.log2S : 125;
+  L.ebits = 128 - keymax > 32 ? 32 : (uint32_t)(128 - keymax);
+  const size_t S = (size_t)1 << L.log2S;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t at = off;
@@ -82,13 +105,21 @@ MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_ac
     return at;
   };
   L.ctrl = take(sizeof(Ctrl));
-  L.table = take(((size_t)1 << L.log2S) * 16);
+  L.table = take(S * 16);
+  L.rep = take(S * 8);
   L.lab0 = take(n * 4);
   L.lab1 = take(n * 4);
-  L.tmp = (p1.stages > 1 || pr.stages > 1) ? take(n * 4) : SIZE_MAX;
-  L.minrep = take(((size_t)1 << L.log2S) * 4);
+  L.tmp = take(n * 4);
+  const size_t warps = moore_max_warps();
+  L.dups = take((n + (warps + 2) * 32) * 4);   // n plus one partial chunk per warp
+  L.wcnt = take(warps * 4);
+  L.minrep = take(S * 4);
   L.flag = take(n);
   L.partials = take(kMaxGrid * 4);
+  L.bm0 = take(S / 8 > 4 ? S / 8 : 4);
+  L.bm1 = take(S / 8 > 4 ? S / 8 : 4);
+  L.seen1 = take(((size_t)1 << L.mbits) / 8);
+  L.seen2 = take(((size_t)1 << L.mbits) / 8);
   L.delta = stage_delta ? take((size_t)k * n * 4) : SIZE_MAX;
   L.accept = stage_accept ? take(n) : SIZE_MAX;
   L.out = stage_out ? take(n * 4) : SIZE_MAX;
@@ -108,17 +139,25 @@ int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, 
   a.k = k;
   a.lab[0] = reinterpret_cast<uint32_t *>(ws + L.lab0);
   a.lab[1] = reinterpret_cast<uint32_t *>(ws + L.lab1);
-  a.tmp = L.tmp == SIZE_MAX ? nullptr : reinterpret_cast<uint32_t *>(ws + L.tmp);
+  a.tmp = reinterpret_cast<uint32_t *>(ws + L.tmp);
   a.table = reinterpret_cast<u128 *>(ws + L.table);
   a.log2S = L.log2S;
   a.minrep = reinterpret_cast<uint32_t *>(ws + L.minrep);
+  a.bm[0] = reinterpret_cast<uint32_t *>(ws + L.bm0);
+  a.bm[1] = reinterpret_cast<uint32_t *>(ws + L.bm1);
+  a.seen1 = reinterpret_cast<uint32_t *>(ws + L.seen1);
+  a.seen2 = reinterpret_cast<uint32_t *>(ws + L.seen2);
+  a.mbits = L.mbits;
+  a.rep = reinterpret_cast<unsigned long long *>(ws + L.rep);
+  a.dups = reinterpret_cast<uint32_t *>(ws + L.dups);
+  a.wcnt = reinterpret_cast<uint32_t *>(ws + L.wcnt);
+  a.wid = L.wid;
+  a.modes = (o.flags & DFA_FLAG_TABLE_ONLY) ? 0u : 3u;
   a.flag = reinterpret_cast<uint8_t *>(ws + L.flag);
   a.partials = reinterpret_cast<uint32_t *>(ws + L.partials);
   a.out = out_dev;
   a.ctrl = reinterpret_cast<Ctrl *>(ws + L.ctrl);
-  a.plan1 = L.plan1;
-  a.planr = L.planr;
-  a.ebits = L.plan1.ebits < L.planr.ebits ? L.plan1.ebits : L.planr.ebits;
+  a.ebits = L.ebits;
   a.max_rounds = o.max_rounds;
   a.timeout_ns = o.timeout_ns;
   a.barrier_ns = o.timeout_ns < 5000000000ull ? o.timeout_ns : 5000000000ull;

@@ -13,9 +13,9 @@ namespace dfa {
 // Byte offsets of the Moore kernel's buffers inside a caller's workspace
 // (SIZE_MAX = absent).
 struct MooreLayout {
-  uint32_t log2S;
-  StagePlan plan1, planr;
-  size_t ctrl, table, lab0, lab1, tmp, minrep, flag, partials, delta, accept, out, total;
+  uint32_t log2S, mbits, wid, ebits;
+  size_t ctrl, table, lab0, lab1, tmp, minrep, flag, partials, bm0, bm1, seen1, seen2, rep, dups, wcnt, delta, accept, out,
+      total;
 };
 
 // Equivalence by union: the two start states whose blocks are compared.

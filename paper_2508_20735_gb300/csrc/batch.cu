@@ -120,7 +120,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &A, const SegInfo &S,
       uint32_t shift = 0;
       if (has_prev) {
         put_bits(key[v], A.tmp[S.state_off + q], 0);
-        shift = bits;
+        shift = P.carry;
       }
       uint32_t j = cbeg;
       if (j == 0) {
@@ -318,8 +318,8 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, std::vector<S
     s.state_off = (uint32_t)st;
     s.log2S = ceil_log2((uint64_t)d.n * 2 < 64 ? 64 : (uint64_t)d.n * 2);
     s.table_off = sl;
-    s.plan1 = make_plan(d.k, 1);
-    s.planr = make_plan(d.k, s.log2S);
+    s.plan1 = make_plan(d.k, 1, s.log2S);
+    s.planr = make_plan(d.k, s.log2S, s.log2S);
     max_stages = std::max({max_stages, s.plan1.stages, s.planr.stages});
     ebits = std::min({ebits, s.plan1.ebits, s.planr.ebits});
     multi |= s.plan1.stages > 1 || s.planr.stages > 1;

@@ -36,6 +36,7 @@ struct Ctrl {
   uint32_t verdict;        // equivalence: 1 = same block
   uint32_t maxed;          // stopped at opts.max_rounds (not an error for the barrier)
   uint32_t qf, qn;         // naivePR: initial leaders (min F, min Q\F)
+  uint32_t ndup;           // filter rounds: states listed for the exact table
   unsigned long long t_start, t_end;
   unsigned long long deadline;  // absolute %globaltimer value
 };

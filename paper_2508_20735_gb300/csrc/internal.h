@@ -12,16 +12,18 @@ struct u128;
 
 // Stage plan for packing a signature of (k+1) components of `bits` bits each
 // into 128-bit keys: stage 0 takes components [0, first); every later stage
-// takes the previous stage's label plus `per` more components.
+// takes the previous stage's label (a table slot, `carry` bits) plus `per`
+// more components.
 struct StagePlan {
   uint32_t bits;    // bits per component
+  uint32_t carry;   // bits of the label carried from one stage to the next
   uint32_t first;   // components in stage 0
   uint32_t per;     // new components per later stage
   uint32_t stages;  // number of stages
   uint32_t ebits;   // epoch bits available in every stage of this plan
 };
 
-StagePlan make_plan(uint32_t k, uint32_t bits);
+__host__ __device__ StagePlan make_plan(uint32_t k, uint32_t bits, uint32_t carry);
 
 // Arguments of the Moore (signature refinement) persistent kernel.  One call
 // refines one state space; a batch or a disjoint union is one state space whose
@@ -35,17 +37,23 @@ struct MooreArgs {
   u128 *table;             // 2^log2S slots
   uint32_t log2S;
   uint32_t *minrep;        // 2^log2S: canonicalisation scratch
+  uint32_t *bm[2];         // direct-mode bitmaps, 2^log2S bits each (ping-pong)
+  uint32_t *seen1, *seen2; // filter-mode 2-bit counters, 2^mbits bits each
+  uint32_t mbits;
+  unsigned long long *rep; // 2^log2S: filter-mode smallest member per table slot
+  uint32_t *dups;          // filter-mode per-warp lists of states in shared buckets
+  uint32_t *wcnt;          // per-warp list lengths
+  uint32_t wid;            // bits of a state number (labels of filter rounds)
   uint8_t *flag;           // n: canonicalisation scratch
   uint32_t *partials;      // gridDim entries
   uint32_t *out;           // n: canonical block numbers
   Ctrl *ctrl;
-  StagePlan plan1;         // round 1 (components are acceptance bits)
-  StagePlan planr;         // rounds >= 2 (components are labels < 2^log2S)
-  uint32_t ebits;          // epoch field width used by every pass
+  uint32_t ebits;          // epoch field width used by every table pass
   uint32_t max_rounds;     // 0 = none
   unsigned long long timeout_ns;  // limit on the whole launch
   unsigned long long barrier_ns;  // limit on one barrier wait
-  uint32_t vec;            // 4: vectorised path (n % 4 == 0), else 1
+  uint32_t vec;            // states per lane in table rounds: 1, 2 or 4
+  uint32_t modes;          // bit 0: allow direct rounds, bit 1: allow filter rounds
   uint32_t stream_delta;   // 1: load δ with evict-first hints (table larger than L2)
   // equivalence by union: stop when these two states separate (if early_exit)
   uint32_t sep_a, sep_b;

@@ -21,11 +21,12 @@ namespace dfa {
 
 static constexpr int kThreads = 512;
 
-StagePlan make_plan(uint32_t k, uint32_t bits) {
+__host__ __device__ StagePlan make_plan(uint32_t k, uint32_t bits, uint32_t carry) {
   StagePlan p{};
   const uint32_t total = k + 1;     // own block + one per letter
   const uint32_t cap = 125;         // key bits; at least 3 bits remain for the epoch
   p.bits = bits;
+  p.carry = carry;
   if ((uint64_t)total * bits <= cap) {
     p.first = total;
     p.per = 1;
@@ -34,9 +35,9 @@ StagePlan make_plan(uint32_t k, uint32_t bits) {
     p.ebits = (128 - used) > 32 ? 32 : (128 - used);
   } else {
     p.first = cap / bits;
-    p.per = cap / bits - 1;
+    p.per = (cap - carry) / bits;
     p.stages = 1 + (total - p.first + p.per - 1) / p.per;
-    const uint32_t used = p.first * bits;
+    const uint32_t used = p.first * bits > carry + p.per * bits ? p.first * bits : carry + p.per * bits;
     p.ebits = (128 - used) > 32 ? 32 : (128 - used);
   }
   return p;
@@ -128,7 +129,7 @@ __device__ __forceinline__ void moore_pass(const MooreArgs &A, const StagePlan &
       load_vec<VEC>(A.tmp + q0, t);
 #pragma unroll
       for (int v = 0; v < VEC; ++v) put_bits(key[v], t[v], 0);
-      shift = bits;
+      shift = P.carry;
     }
     uint32_t j = cbeg;
     if (j == 0) {
@@ -187,12 +188,229 @@ __device__ __forceinline__ void clear_table(u128 *table, uint32_t log2S) {
   }
 }
 
+// ----------------------------------------------------------------- direct rounds
+// When the whole signature fits in K <= log2 S bits, the packed signature is
+// itself the new label: no table, no hash.  A bitmap over the 2^K possible
+// signatures tells whether a signature is new (the first atomicOr to set its
+// bit counts one block).  Signatures of at most 13 bits are first collected in
+// a per-block bitmap in shared memory and merged once per block.
+template <bool ROUND1>
+__device__ __forceinline__ void direct_pass(const MooreArgs &A, uint32_t w, uint32_t K, const uint32_t *__restrict__ src,
+                                            uint32_t *__restrict__ dst, uint32_t *bm, uint32_t &local_new,
+                                            uint32_t &seen, uint32_t *sbm) {
+  const uint32_t n = A.n, k = A.k;
+  const bool small = K <= 13;
+  const uint32_t swords = small ? ((1u << K) + 31) / 32 : 0;
+  if (small) {
+    for (uint32_t i = threadIdx.x; i < swords; i += blockDim.x) sbm[i] = 0u;
+    __syncthreads();
+  }
+  const unsigned long long keep = policy_evict_last(), drop = policy_evict_first();
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint64_t base = (uint64_t)gwarp * 32; base < n; base += (uint64_t)nwarps * 32) {
+    const uint32_t q0 = (uint32_t)base + lane;
+    const bool valid = q0 < n;
+    const uint32_t q = valid ? q0 : 0u;
+    uint32_t key;
+    if (ROUND1) {
+      key = A.accept[q] != 0;
+      if (valid) seen |= key ? 1u : 2u;
+    } else {
+      key = src[q];
+    }
+    uint32_t shift = w;
+    for (uint32_t a = 0; a < k; ++a) {
+      const uint32_t *row = A.delta + (size_t)a * n;
+      uint32_t d = A.stream_delta ? ld_u32_stream(row + q, drop) : row[q];
+      if (ROUND1 && d >= n) {
+        if (valid) atomicOr(&A.ctrl->err, ERR_BAD_DELTA);
+        d = 0;
+      }
+      const uint32_t c = ROUND1 ? (uint32_t)(A.accept[d] != 0) : ld_u32_hint(src + d, keep);
+      key |= c << shift;
+      shift += w;
+    }
+    if (valid) st_u32_hint(dst + q, key, drop);
+    const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, valid ? key : 0xFFFFFFFFu) & vm;
+    if (valid && lane == (uint32_t)(__ffs(grp) - 1)) {
+      const uint32_t bit = 1u << (key & 31u);
+      if (small) {
+        atomicOr(&sbm[key >> 5], bit);
+      } else {
+        const uint32_t old = atomicOr(&bm[key >> 5], bit);
+        if (!(old & bit)) ++local_new;
+      }
+    }
+  }
+  if (small) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < swords; i += blockDim.x) {
+      const uint32_t v = sbm[i];
+      if (v) {
+        const uint32_t old = atomicOr(&bm[i], v);
+        local_new += __popc(v & ~old);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------- filter rounds
+// Rounds in which most signatures are unique.  Pass A hashes every signature
+// into an L2-resident array of 2-bit saturating counters (two bitmaps).  A
+// signature alone in its bucket is unique, so its state forms a block by
+// itself and is labelled with its own number (pass B).  Only signatures in
+// shared buckets go through the exact table; each such block is labelled with
+// its smallest member, kept per slot with a 64-bit atomicMax on
+// (round << 32 | ~state) (pass B), and read back in pass C.  Labels of these
+// rounds are state numbers, wid bits wide.
+__device__ __forceinline__ u128 pack_key(const MooreArgs &A, uint32_t w, const uint32_t *__restrict__ src, uint32_t q,
+                                         unsigned long long keep, unsigned long long drop) {
+  const uint32_t n = A.n, k = A.k;
+  u128 key{0ull, 0ull};
+  put_bits(key, src[q], 0);
+  uint32_t shift = w;
+  for (uint32_t a = 0; a < k; ++a) {
+    const uint32_t *row = A.delta + (size_t)a * n;
+    const uint32_t d = A.stream_delta ? ld_u32_stream(row + q, drop) : row[q];
+    put_bits(key, ld_u32_hint(src + d, keep), shift);
+    shift += w;
+  }
+  return key;
+}
+
+// Pass A: hash every signature (a 64-bit hash built component by component;
+// the packed key is not needed here) into the counters.  A bucket with count
+// one proves its signature unique whatever the hash, since equal signatures
+// hash alike; hash quality only affects how many unique signatures are sent
+// on to the exact table.
+__device__ __forceinline__ unsigned long long hash_step(unsigned long long h, uint32_t c) {
+  h = (h ^ c) * 0x9E3779B97F4A7C15ull;
+  return h ^ (h >> 29);
+}
+
+__device__ __forceinline__ void filter_pass_a(const MooreArgs &A, const uint32_t *__restrict__ src) {
+  const uint32_t n = A.n, k = A.k;
+  const unsigned long long keep = policy_evict_last(), drop = policy_evict_first();
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (uint32_t q = tid; q < n; q += stride) {
+    unsigned long long h = hash_step(0x243F6A8885A308D3ull, src[q]);
+    for (uint32_t a = 0; a < k; ++a) {
+      const uint32_t *row = A.delta + (size_t)a * n;
+      const uint32_t d = A.stream_delta ? ld_u32_stream(row + q, drop) : row[q];
+      h = hash_step(h, ld_u32_hint(src + d, keep));
+    }
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    const uint32_t b = (uint32_t)(h >> (64 - A.mbits));
+    const uint32_t bit = 1u << (b & 31u);
+    const uint32_t old = atomicOr(&A.seen1[b >> 5], bit);
+    if (old & bit) atomicOr(&A.seen2[b >> 5], bit);
+    A.tmp[q] = b;
+  }
+}
+
+// The listed states of a filter round live in per-warp slices of `dups`: warp
+// g owns [g*cap, g*cap + count_g), cap = ceil(states per warp / 32) * 32, and
+// appends with a register cursor (no global atomics).  Passes D and C walk the
+// same slices with the same warps.
+__device__ __forceinline__ uint32_t dup_cap(uint32_t n, uint32_t nwarps) {
+  const uint32_t chunks = (n + 31) / 32;
+  return (chunks + nwarps - 1) / nwarps * 32;
+}
+
+// Pass B: a signature alone in its bucket is unique: its state becomes a
+// singleton block labelled with its own number.  The others are listed.
+__device__ __forceinline__ void filter_pass_b(const MooreArgs &A, uint32_t *__restrict__ dst, uint32_t &local_new) {
+  const uint32_t n = A.n;
+  const unsigned long long drop = policy_evict_first();
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  uint32_t *list = A.dups + (size_t)gwarp * dup_cap(n, nwarps);
+  uint32_t cursor = 0;
+  for (uint64_t base = (uint64_t)gwarp * 32; base < n; base += (uint64_t)nwarps * 32) {
+    const uint32_t q = (uint32_t)base + lane;
+    const bool valid = q < n;
+    bool dup = false;
+    if (valid) {
+      const uint32_t b = A.tmp[q];
+      dup = (A.seen2[b >> 5] >> (b & 31u)) & 1u;
+      if (!dup) {
+        st_u32_hint(dst + q, q, drop);
+        ++local_new;
+      }
+    }
+    const unsigned dm = __ballot_sync(0xFFFFFFFFu, dup);
+    if (dup) list[cursor + __popc(dm & ((1u << lane) - 1u))] = q;
+    cursor += __popc(dm);
+  }
+  if (lane == 0) A.wcnt[gwarp] = cursor;
+}
+
+// Pass D: the listed states insert their exact keys; each slot keeps its
+// smallest member via atomicMax on (round << 32 | ~state), one atomic per
+// (warp, slot).
+__device__ __forceinline__ void filter_pass_d(const MooreArgs &A, uint32_t w, const uint32_t *__restrict__ src,
+                                              uint32_t epoch, uint32_t r, CtaCache *cache) {
+  const unsigned long long keep = policy_evict_last(), drop = policy_evict_first();
+  const unsigned long long etag = (unsigned long long)epoch << (64 - A.ebits);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t *list = A.dups + (size_t)gwarp * dup_cap(A.n, nwarps);
+  const uint32_t nd = A.wcnt[gwarp];
+  for (uint32_t base = 0; base < nd; base += 32) {
+    const uint32_t i = base + lane;
+    const bool valid = i < nd;
+    const uint32_t q = valid ? list[i] : 0u;
+    u128 key[1];
+    key[0] = pack_key(A, w, src, q, keep, drop);
+    key[0].hi |= etag;
+    uint32_t slot[1];
+    uint32_t created = 0;
+    warp_insert<1>(A.table, A.log2S, key, valid, A.ebits, epoch, slot, created, &A.ctrl->err, cache);
+    if (valid) A.tmp[q] = slot[0];
+    // listed states are ascending within the slice, so the lowest lane of a
+    // slot group holds the group's smallest state
+    const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+    const unsigned sg = __match_any_sync(0xFFFFFFFFu, valid ? slot[0] : 0xFFFFFFFFu) & vm;
+    if (valid && lane == (uint32_t)(__ffs(sg) - 1))
+      atomicMax(&A.rep[slot[0]], ((unsigned long long)r << 32) | (unsigned long long)(~q));
+  }
+}
+
+// Pass C: listed states read their block's smallest member; the counters are
+// cleared for the next filter round.
+__device__ __forceinline__ void filter_pass_c(const MooreArgs &A, uint32_t *__restrict__ dst, uint32_t &local_new) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t gwarp = tid >> 5, nwarps = stride >> 5;
+  const uint32_t *list = A.dups + (size_t)gwarp * dup_cap(A.n, nwarps);
+  const uint32_t nd = A.wcnt[gwarp];
+  for (uint32_t i = lane; i < nd; i += 32) {
+    const uint32_t q = list[i];
+    const uint32_t rep = ~(uint32_t)A.rep[A.tmp[q]];
+    dst[q] = rep;
+    if (rep == q) ++local_new;
+  }
+  const size_t words = ((size_t)1 << A.mbits) / 32;
+  for (size_t i = tid; i < words; i += stride) {
+    A.seen1[i] = 0u;
+    A.seen2[i] = 0u;
+  }
+}
+
+enum : uint32_t { MODE_DIRECT = 0, MODE_TABLE = 1, MODE_FILTER = 2 };
+
 template <int VEC>
-__global__ void __launch_bounds__(kThreads) moore_kernel(MooreArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
   __shared__ uint32_t s_red[kThreads / 32];
   __shared__ CtaCache cache;
+  __shared__ uint32_t sbm[(1u << 13) / 32];
   Ctrl *C = A.ctrl;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   if (leader) {
     const unsigned long long t = gtimer();
     C->t_start = t;
@@ -200,8 +418,11 @@ __global__ void __launch_bounds__(kThreads) moore_kernel(MooreArgs A) {
     C->sep_round = 0xFFFFFFFFu;
   }
   const uint32_t emax = A.ebits >= 32 ? 0xFFFFFFFFu : ((1u << A.ebits) - 1u);
+  const size_t S = (size_t)1 << A.log2S;
   uint32_t epoch = 0, r = 0, changed = 0, B_prev = 0, final_buf = 0, B_final = 0xFFFFFFFFu;
-  bool ok = true, separated = false, skip = false;
+  uint32_t w = 1;              // bits of the labels the next round reads (round 0: acceptance bits)
+  uint32_t final_space = 2;    // label space of the final labels
+  bool ok = true, separated = false, skip = false, table_clean = false;
 
   // Equivalence by union: the empty word already separates start states that
   // differ in acceptance (round 0).
@@ -210,20 +431,40 @@ __global__ void __launch_bounds__(kThreads) moore_kernel(MooreArgs A) {
     if (leader) C->sep_round = 0;
     if (A.early_exit) {
       skip = true;   // the answer needs no round; report the initial partition
-      const uint32_t stride = gridDim.x * blockDim.x;
-      for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < A.n; q += stride)
-        A.lab[0][q] = A.accept[q] != 0;
+      for (uint32_t q = tid; q < A.n; q += stride) A.lab[0][q] = A.accept[q] != 0;
     }
   }
-  if (!skip) clear_table(A.table, A.log2S);
+  // direct bitmap of round 1 and the filter counters start clean
+  for (size_t i = tid; i < S / 32; i += stride) A.bm[1][i] = 0u;
+  for (size_t i = tid; i < ((size_t)1 << A.mbits) / 32; i += stride) {
+    A.seen1[i] = 0u;
+    A.seen2[i] = 0u;
+  }
   ok = grid_sync(C, A.barrier_ns);
   for (r = 1; ok && !skip; ++r) {
     const bool round1 = r == 1;
-    const StagePlan &P = round1 ? A.plan1 : A.planr;
     const uint32_t *src = A.lab[(r - 1) & 1];
     uint32_t *dst = A.lab[r & 1];
+    const uint64_t K = (uint64_t)(A.k + 1) * w;
+    uint32_t mode = MODE_TABLE;
+    if ((A.modes & 1u) && K <= A.log2S && K <= 27) mode = MODE_DIRECT;
+    else if ((A.modes & 2u) && !round1 && K <= 125 && (uint64_t)B_prev * 64 >= A.n) mode = MODE_FILTER;
+    if (mode != MODE_DIRECT && !table_clean) {   // first table round: the table and slot owners start clean
+      clear_table(A.table, A.log2S);
+      for (size_t i = tid; i < S; i += stride) A.rep[i] = 0ull;
+      ok = grid_sync(C, A.barrier_ns);
+      if (!ok) break;
+      table_clean = true;
+    }
+    // the bitmap the next round would use starts clean
+    for (size_t i = tid; i < S / 32; i += stride) A.bm[(r + 1) & 1][i] = 0u;
     uint32_t local_new = 0, seen = 0;
-    for (uint32_t s = 0; s < P.stages && ok; ++s) {
+    if (mode == MODE_DIRECT) {
+      if (round1) direct_pass<true>(A, w, (uint32_t)K, src, dst, A.bm[r & 1], local_new, seen, sbm);
+      else direct_pass<false>(A, w, (uint32_t)K, src, dst, A.bm[r & 1], local_new, seen, sbm);
+      w = (uint32_t)K;
+      final_space = 1u << K;
+    } else if (mode == MODE_FILTER) {
       if (epoch == emax) {
         clear_table(A.table, A.log2S);
         ok = grid_sync(C, A.barrier_ns);
@@ -231,12 +472,38 @@ __global__ void __launch_bounds__(kThreads) moore_kernel(MooreArgs A) {
         if (!ok) break;
       }
       ++epoch;
-      const bool last = s + 1 == P.stages;
-      if (round1) moore_pass<VEC, true>(A, P, s, src, dst, last, epoch, local_new, seen, &cache);
-      else moore_pass<VEC, false>(A, P, s, src, dst, last, epoch, local_new, seen, &cache);
-      if (!last) ok = grid_sync(C, A.barrier_ns);
+      filter_pass_a(A, src);
+      ok = grid_sync(C, A.barrier_ns);
+      if (!ok) break;
+      filter_pass_b(A, dst, local_new);
+      ok = grid_sync(C, A.barrier_ns);
+      if (!ok) break;
+      cta_cache_clear(&cache);
+      filter_pass_d(A, w, src, epoch, r, &cache);
+      ok = grid_sync(C, A.barrier_ns);
+      if (!ok) break;
+      filter_pass_c(A, dst, local_new);
+      w = A.wid;
+      final_space = A.n;
+    } else {
+      const StagePlan P = make_plan(A.k, w, A.log2S);
+      for (uint32_t s = 0; s < P.stages && ok; ++s) {
+        if (epoch == emax) {
+          clear_table(A.table, A.log2S);
+          ok = grid_sync(C, A.barrier_ns);
+          epoch = 0;
+          if (!ok) break;
+        }
+        ++epoch;
+        const bool last = s + 1 == P.stages;
+        if (round1) moore_pass<VEC, true>(A, P, s, src, dst, last, epoch, local_new, seen, &cache);
+        else moore_pass<VEC, false>(A, P, s, src, dst, last, epoch, local_new, seen, &cache);
+        if (!last) ok = grid_sync(C, A.barrier_ns);
+      }
+      if (!ok) break;
+      w = A.log2S;
+      final_space = (uint32_t)S;
     }
-    if (!ok) break;
     const uint32_t bnew = block_sum(local_new, s_red);
     if (threadIdx.x == 0 && bnew) atomicAdd(&C->cnt[r % 3], bnew);
     if (round1) {
@@ -276,7 +543,8 @@ __global__ void __launch_bounds__(kThreads) moore_kernel(MooreArgs A) {
       C->rounds_executed = r;
       C->rounds_changed = changed;
     }
-    ok = canonicalise(CanonArgs{A.n, A.lab[final_buf], (size_t)1 << A.log2S, A.minrep, A.flag, A.partials, A.out,
+    const size_t space = skip ? 2 : final_space;
+    ok = canonicalise(CanonArgs{A.n, A.lab[final_buf], space < S ? space : S, A.minrep, A.flag, A.partials, A.out,
                                 A.ctrl, A.barrier_ns},
                       B_final, s_red);
   }

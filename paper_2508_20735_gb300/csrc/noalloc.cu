@@ -24,9 +24,10 @@
 
 namespace dfa {
 
-// 4 MiB: enough for the Moore kernel's scratch at DFA_NOALLOC_MAX_STATES states
-// (table 2 MiB, labels 3 x 256 KiB, canonical-numbering scratch 0.6 MiB).
-static constexpr size_t kNoallocScratchBytes = 4u << 20;
+// 8 MiB: enough for the Moore kernel's scratch at DFA_NOALLOC_MAX_STATES states
+// (table 2 MiB, slot owners 1 MiB, labels 3 x 256 KiB, bitmaps 0.3 MiB,
+// canonical-numbering scratch 0.6 MiB).
+static constexpr size_t kNoallocScratchBytes = 8u << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 static constexpr int kMaxDevices = 64;

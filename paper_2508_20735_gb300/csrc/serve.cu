@@ -102,7 +102,7 @@ __device__ __forceinline__ void serve_tile(const StepArgs &A, const ServeSeg &S,
     uint32_t shift = 0;
     if (has_prev) {
       put_bits(key[0], S.tmp[q], 0);
-      shift = bits;
+      shift = P.carry;
     }
     uint32_t j = cbeg;
     if (j == 0) {
@@ -262,8 +262,8 @@ static size_t req_layout(Req &r) {
   };
   const uint64_t n = r.n;
   r.log2S = ceil_log2(n * 2 < 64 ? 64 : n * 2);
-  r.p1 = make_plan(r.k, 1);
-  r.pr = make_plan(r.k, r.log2S);
+  r.p1 = make_plan(r.k, 1, r.log2S);
+  r.pr = make_plan(r.k, r.log2S, r.log2S);
   r.ebits = std::min(r.p1.ebits, r.pr.ebits);
   r.o_err = take(4);
   r.o_delta = take((size_t)r.k * n * 4);

@@ -40,7 +40,8 @@ def _batch(g, dfas, schedule=-1, host=False, **kw):
 def _mixed():
     dfas = [dfagen.random_dfa(n, k, p, 900 + i) for i, (n, k, p) in enumerate(
         [(1, 2, 0.5), (2, 1, 0.5), (3, 0, 0.5), (5, 3, 0.5), (64, 2, 0.3), (257, 4, 0.3), (1000, 8, 0.3),
-         (3000, 40, 0.5), (4096, 2, 0.0), (777, 3, 1.0), (10_000, 5, 0.3)])]
+         (3000, 40, 0.5), (4096, 2, 0.0), (777, 3, 1.0), (10_000, 5, 0.3), (14_462, 8, 0.3),
+         (300, 130, 0.5)])]
     dfas.append(dfagen.fibonacci_dfa(11))
     dfas.append(dfagen.bit_splitter(9))
     base = dfagen.random_dfa(300, 3, 0.5, 61)

@@ -64,13 +64,22 @@ def test_vector_widths(g, schedule, n, k):
     _assert_parity(g, A, schedule=schedule)
 
 
+@pytest.mark.parametrize("n,k,seed", [(10_000, 2, 1), (300_000, 4, 2), (65_536, 3, 3), (4097, 8, 4)])
+def test_table_only_path(g, n, k, seed):
+    """Renumbering through the exact table in every round (no direct or filter
+    rounds) gives the same partition and round counts."""
+    A = dfagen.random_dfa(n, k, 0.5, seed)
+    _assert_parity(g, A, flags=g.DFA_FLAG_TABLE_ONLY)
+
+
 @pytest.mark.parametrize("p", [0.0, 1.0, 0.01, 0.3, 0.9])
 def test_acceptance_extremes(g, p):
     A = dfagen.random_dfa(5000, 3, p, 7)
     _assert_parity(g, A)
 
 
-@pytest.mark.parametrize("n,k", [(10_000, 8), (20_000, 12), (3000, 40), (777, 100)])
+@pytest.mark.parametrize("n,k", [(10_000, 8), (20_000, 12), (3000, 40), (777, 100), (14_462, 8), (300, 130),
+                                 (1000, 200)])
 def test_multi_stage_keys(g, n, k):
     """Signatures wider than one 128-bit key are renumbered in several exact stages."""
     A = dfagen.random_dfa(n, k, 0.5, n + k)
@@ -141,6 +150,12 @@ def test_deterministic(g):
 def test_large_random_2p22(g):
     """A quarter of the 2^24-state workload, compared in full with the oracle."""
     A = dfagen.random_dfa(1 << 22, 4, 0.5, 2)
+    _assert_parity(g, A)
+
+
+def test_bench_workload_2p24(g):
+    """The bench workload itself (2^24 states, 4 letters, seed 2), in full."""
+    A = dfagen.random_dfa(1 << 24, 4, 0.5, 2)
     _assert_parity(g, A)
 
 
