@@ -120,6 +120,9 @@ MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_ac
   L.bm1 = take(S / 8 > 4 ? S / 8 : 4);
   L.seen1 = take(((size_t)1 << L.mbits) / 8);
   L.seen2 = take(((size_t)1 << L.mbits) / 8);
+  L.seen3 = take(((size_t)1 << L.mbits) / 16);
+  L.seen4 = take(((size_t)1 << L.mbits) / 16);
+  L.tmp2 = take(n * 4);
   L.delta = stage_delta ? take((size_t)k * n * 4) : SIZE_MAX;
   L.accept = stage_accept ? take(n) : SIZE_MAX;
   L.out = stage_out ? take(n * 4) : SIZE_MAX;
@@ -147,6 +150,9 @@ int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, 
   a.bm[1] = reinterpret_cast<uint32_t *>(ws + L.bm1);
   a.seen1 = reinterpret_cast<uint32_t *>(ws + L.seen1);
   a.seen2 = reinterpret_cast<uint32_t *>(ws + L.seen2);
+  a.seen3 = reinterpret_cast<uint32_t *>(ws + L.seen3);
+  a.seen4 = reinterpret_cast<uint32_t *>(ws + L.seen4);
+  a.tmp2 = reinterpret_cast<uint32_t *>(ws + L.tmp2);
   a.mbits = L.mbits;
   a.rep = reinterpret_cast<unsigned long long *>(ws + L.rep);
   a.dups = reinterpret_cast<uint32_t *>(ws + L.dups);

@@ -39,6 +39,8 @@ struct MooreArgs {
   uint32_t *minrep;        // 2^log2S: canonicalisation scratch
   uint32_t *bm[2];         // direct-mode bitmaps, 2^log2S bits each (ping-pong)
   uint32_t *seen1, *seen2; // filter-mode 2-bit counters, 2^mbits bits each
+  uint32_t *seen3, *seen4; // second filter over listed states, 2^(mbits-1) bits each
+  uint32_t *tmp2;          // n: second-filter bucket per state
   uint32_t mbits;
   unsigned long long *rep; // 2^log2S: filter-mode smallest member per table slot
   uint32_t *dups;          // filter-mode per-warp lists of states in shared buckets

@@ -309,6 +309,10 @@ __device__ __forceinline__ void filter_pass_a(const MooreArgs &A, const uint32_t
     const uint32_t old = atomicOr(&A.seen1[b >> 5], bit);
     if (old & bit) atomicOr(&A.seen2[b >> 5], bit);
     A.tmp[q] = b;
+    // an independent bucket for the second filter (states listed by pass B)
+    unsigned long long h2 = (h ^ 0x9E3779B97F4A7C15ull) * 0xc4ceb9fe1a85ec53ull;
+    h2 ^= h2 >> 31;
+    A.tmp2[q] = (uint32_t)(h2 >> (64 - (A.mbits - 1)));
   }
 }
 
@@ -346,6 +350,56 @@ __device__ __forceinline__ void filter_pass_b(const MooreArgs &A, uint32_t *__re
     if (dup) list[cursor + __popc(dm & ((1u << lane) - 1u))] = q;
     cursor += __popc(dm);
   }
+  if (lane == 0) {
+    A.wcnt[gwarp] = cursor;
+    if (cursor) atomicAdd(&A.ctrl->ndup, cursor);
+  }
+}
+
+// Passes E and F: a second filter over the listed states only, with an
+// independent bucket of A.mbits - 1 bits.  Most listed signatures merely
+// collided with another one in the first filter; alone in their second bucket
+// they are unique too (pass F labels them with their state number and keeps
+// the rest listed, compacted in place within the warp's slice).
+__device__ __forceinline__ void filter_pass_e(const MooreArgs &A) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t *list = A.dups + (size_t)gwarp * dup_cap(A.n, nwarps);
+  const uint32_t nd = A.wcnt[gwarp];
+  for (uint32_t i = lane; i < nd; i += 32) {
+    const uint32_t b = A.tmp2[list[i]];
+    const uint32_t bit = 1u << (b & 31u);
+    const uint32_t old = atomicOr(&A.seen3[b >> 5], bit);
+    if (old & bit) atomicOr(&A.seen4[b >> 5], bit);
+  }
+}
+
+__device__ __forceinline__ void filter_pass_f(const MooreArgs &A, uint32_t *__restrict__ dst, uint32_t &local_new) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  uint32_t *list = A.dups + (size_t)gwarp * dup_cap(A.n, nwarps);
+  const uint32_t nd = A.wcnt[gwarp];
+  uint32_t cursor = 0;
+  for (uint32_t base = 0; base < nd; base += 32) {
+    const uint32_t i = base + lane;
+    const bool valid = i < nd;
+    bool still = false;
+    uint32_t q = 0;
+    if (valid) {
+      q = list[i];
+      const uint32_t b = A.tmp2[q];
+      still = (A.seen4[b >> 5] >> (b & 31u)) & 1u;
+      if (!still) {
+        dst[q] = q;
+        ++local_new;
+      }
+    }
+    // every lane has read its entry before any lane writes (positions <= reads)
+    const unsigned sm = __ballot_sync(0xFFFFFFFFu, still);
+    if (still) list[cursor + __popc(sm & ((1u << lane) - 1u))] = q;
+    cursor += __popc(sm);
+  }
+  __syncwarp();
   if (lane == 0) A.wcnt[gwarp] = cursor;
 }
 
@@ -399,6 +453,10 @@ __device__ __forceinline__ void filter_pass_c(const MooreArgs &A, uint32_t *__re
     A.seen1[i] = 0u;
     A.seen2[i] = 0u;
   }
+  for (size_t i = tid; i < words / 2; i += stride) {
+    A.seen3[i] = 0u;
+    A.seen4[i] = 0u;
+  }
 }
 
 enum : uint32_t { MODE_DIRECT = 0, MODE_TABLE = 1, MODE_FILTER = 2 };
@@ -423,6 +481,7 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
   uint32_t w = 1;              // bits of the labels the next round reads (round 0: acceptance bits)
   uint32_t final_space = 2;    // label space of the final labels
   bool ok = true, separated = false, skip = false, table_clean = false;
+  bool filter_ok = true;       // cleared for good once a filter round lists most states
 
   // Equivalence by union: the empty word already separates start states that
   // differ in acceptance (round 0).
@@ -440,6 +499,10 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
     A.seen1[i] = 0u;
     A.seen2[i] = 0u;
   }
+  for (size_t i = tid; i < ((size_t)1 << A.mbits) / 64; i += stride) {
+    A.seen3[i] = 0u;
+    A.seen4[i] = 0u;
+  }
   ok = grid_sync(C, A.barrier_ns);
   for (r = 1; ok && !skip; ++r) {
     const bool round1 = r == 1;
@@ -448,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
     const uint64_t K = (uint64_t)(A.k + 1) * w;
     uint32_t mode = MODE_TABLE;
     if ((A.modes & 1u) && K <= A.log2S && K <= 27) mode = MODE_DIRECT;
-    else if ((A.modes & 2u) && !round1 && K <= 125 && (uint64_t)B_prev * 64 >= A.n) mode = MODE_FILTER;
+    else if ((A.modes & 2u) && filter_ok && !round1 && K <= 125 && (uint64_t)B_prev * 64 >= A.n) mode = MODE_FILTER;
     if (mode != MODE_DIRECT && !table_clean) {   // first table round: the table and slot owners start clean
       clear_table(A.table, A.log2S);
       for (size_t i = tid; i < S; i += stride) A.rep[i] = 0ull;
@@ -476,6 +539,14 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
       ok = grid_sync(C, A.barrier_ns);
       if (!ok) break;
       filter_pass_b(A, dst, local_new);
+      ok = grid_sync(C, A.barrier_ns);
+      if (!ok) break;
+      // mostly true duplicates (large blocks): later rounds use the table path
+      if ((uint64_t)ld_relaxed(&C->ndup) * 2 > A.n) filter_ok = false;
+      filter_pass_e(A);
+      ok = grid_sync(C, A.barrier_ns);
+      if (!ok) break;
+      filter_pass_f(A, dst, local_new);
       ok = grid_sync(C, A.barrier_ns);
       if (!ok) break;
       cta_cache_clear(&cache);
@@ -517,7 +588,10 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
     if (!ok) break;
     const uint32_t B_r = ld_relaxed(&C->cnt[r % 3]);
     if (round1) B_prev = (ld_relaxed(&C->seen_acc) != 0u) + (ld_relaxed(&C->seen_rej) != 0u);
-    if (leader) C->cnt[(r + 2) % 3] = 0u;
+    if (leader) {
+      C->cnt[(r + 2) % 3] = 0u;
+      C->ndup = 0u;   // read only inside a filter round, after its pass B
+    }
     final_buf = r & 1;
     B_final = B_r;
     const bool grew = B_r != B_prev;
