@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the CPU-oracle leg (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads (batch, chain, serve)")
     return ap.parse_args()
 
 
@@ -155,6 +156,100 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+
+
+def _dev(A):
+    import numpy as np
+    import torch
+    return (torch.from_numpy(np.ascontiguousarray(A.delta).view(np.int32)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(A.accept)).cuda())
+
+
+def _time_calls(fn, reps):
+    import torch
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t) / reps
+
+
+def extras(g):
+    """The other workloads of the hot path, measured after the headline (not part of it)."""
+    import numpy as np
+    import torch
+
+    import dfagen
+    out = {}
+    # random DFA, n = 10,000, k = 2 (small: latency-bound)
+    A = dfagen.random_dfa(10_000, 2, 0.5, 1)
+    d, a = _dev(A)
+    res = g.minimise(d, a)[1]
+    dev = []
+    for _ in range(20):
+        dev.append(g.minimise(d, a)[1].device_ns)
+    out["random_n1e4_k2"] = {"device_us": statistics.median(dev) / 1e3, "rounds": res.rounds_executed,
+                             "transitions_per_s": A.n * A.k * res.rounds_executed / (statistics.median(dev) * 1e-9)}
+    # deep-round chain, n = 2^20: transPR in full; plain refinement over a bounded number of rounds
+    C = dfagen.chain_dfa(1 << 20)
+    d, a = _dev(C)
+    g.minimise(d, a, algo="trans")
+    tr = g.minimise(d, a, algo="trans")[1]
+    bounded = 20_000
+    mo = g.minimise(d, a, max_rounds=bounded, check=False)[1]
+    us_round = mo.device_ns / 1e3 / mo.rounds_executed
+    out["chain_n2p20"] = {
+        "trans": {"rounds": tr.rounds_executed, "device_ms": tr.device_ns / 1e6, "blocks": tr.num_blocks},
+        "moore": {"rounds_needed": C.n - 1, "rounds_timed": mo.rounds_executed, "us_per_round": us_round,
+                  "projected_s_for_all_rounds": us_round * (C.n - 1) / 1e6},
+    }
+    # batch of 4,096 DFAs: one launch vs one dfa_minimise per DFA
+    dfas = dfagen.batch_dfas(4096, 64, 65_536, 2, 8, 0.3, 4)
+    items = [_dev(X) for X in dfas]
+    outb = torch.empty(sum(X.n for X in dfas), dtype=torch.int32, device="cuda")
+    g.minimise_batch(items, out=outb)   # autotune on first use
+    tb = _time_calls(lambda: g.minimise_batch(items, out=outb), 3)
+    singles = [(x[0], x[1], torch.empty(x[1].numel(), dtype=torch.int32, device="cuda")) for x in items]
+    ts = _time_calls(lambda: [g.minimise(x[0], x[1], out=x[2]) for x in singles], 1)
+    trans = sum(X.n * X.k for X in dfas)
+    out["batch_4096"] = {"states": int(sum(X.n for X in dfas)), "batched_dfas_per_s": 4096 / tb,
+                         "single_launch_dfas_per_s": 4096 / ts, "speedup": ts / tb, "batched_ms": tb * 1e3}
+    # served equivalence stream (bounded sample: requests drawn from a pool of generated pairs)
+    pool = [dfagen.equivalence_pair(i, 5) for i in range(24)]
+    nreq = 400
+    with g.Server(24 << 30, max_slots=64) as srv:
+        t0 = time.perf_counter()
+        tickets = [srv.submit_equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start))
+                   for A, B, _ in (pool[i % len(pool)] for i in range(nreq))]
+        for t in tickets:
+            srv.wait(t)
+        cap = nreq / (time.perf_counter() - t0)
+    rng = np.random.default_rng(5)
+    lam = 0.8 * cap
+    gaps = rng.exponential(1.0 / lam, nreq)
+    wrong = 0
+    with g.Server(24 << 30, max_slots=64) as srv:
+        tickets = []
+        t_next = time.perf_counter()
+        for i in range(nreq):
+            t_next += gaps[i]
+            while time.perf_counter() < t_next:
+                pass
+            A, B, _ = pool[i % len(pool)]
+            tickets.append(srv.submit_equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start)))
+        for i, t in enumerate(tickets):
+            st, _, eq, _ = srv.wait(t)
+            wrong += int(bool(eq) != pool[i % len(pool)][2])
+        s = srv.stats()
+    out["serve_equiv"] = {"requests": nreq, "distinct_pairs": len(pool), "closed_loop_rps": cap,
+                          "offered_rps": lam, "p50_us": s["p50_us"], "p99_us": s["p99_us"],
+                          "throughput_rps": s["throughput_rps"], "wrong_verdicts": wrong,
+                          "sample": "Poisson arrivals at 0.8 x closed-loop capacity; pairs of the served-equivalence "
+                                    "recipe (A: n log-uniform in [1e3, 1e6], k in {2, 4}) reused round robin"}
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -231,15 +326,17 @@ def main():
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                 "traffic": None, "kernel": "dfa::moore_kernel",
                 "algorithmic_bytes_per_launch": algo_bytes, "kernel_ms": kernel_s * 1e3}
-    prof = os.path.join(ROOT, "profiles", "moore_kernel_random_n2p24_k4.json")
+    prof = os.path.join(ROOT, "profiles", "moore_kernel_traffic_random_n2p24_k4.txt")
     if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                pj = json.load(f)
-            if pj.get("kernel_source_hash") == kernel_source_hash():
-                roofline["traffic"] = pj["dram_bytes_per_launch"]
-        except Exception:
-            pass
+        fields = {}
+        with open(prof) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    key, val = line.split(":", 1)
+                    fields[key.strip()] = val.strip()
+        # the figure is null once the kernel sources have changed since it was measured
+        if fields.get("kernel_source_hash") == kernel_source_hash():
+            roofline["traffic"] = int(fields["dram_bytes_per_launch"])
 
     # end to end through the same C call with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -277,6 +374,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(A)
+    ex = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        del ws
+        torch.cuda.empty_cache()
+        ex = extras(g)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -286,7 +388,7 @@ def main():
                                l2="inputs larger than L2 (delta 256 MiB)",
                                parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps,
-                "roofline": roofline, "cpu_baseline": cpu}
+                "roofline": roofline, "cpu_baseline": cpu, "extras": ex}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
