@@ -116,6 +116,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def whole_job(units: float, elapsed_s: float, dist=None, device="cpu"):
+    """Whole-job throughput over ranks: the units every rank processed divided
+    by the slowest rank's time (every rank gets the same value)."""
+    if dist is None:
+        return units / elapsed_s, elapsed_s
+    import torch
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 def cpu_baseline(A, seconds_hint=True):
     """The oracle as it stands, one Moore round on the full workload (a bounded sample)."""
     import numpy as np
@@ -309,12 +322,9 @@ def main():
         ev1.record(stream)
         barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
     trans = n * k * sum(rounds)
-    value = trans * world / (elapsed_ms * 1e-3)
+    value, elapsed_s = whole_job(trans, elapsed_ms * 1e-3, dist, "cuda")
+    elapsed_ms = elapsed_s * 1e3
     ms_per_step = elapsed_ms / args.steps
 
     # roofline of the refinement kernel: (4k+8)*n algorithmic bytes per round
@@ -362,12 +372,8 @@ def main():
         for _ in range(args.steps):
             er.append(hstep().rounds_executed)
         barrier()
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": n * k * sum(er) * world / e2e_s, "unit": UNIT,
+        e2e_val, _ = whole_job(n * k * sum(er), time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": e2e_val, "unit": UNIT,
                "h2d_bytes_per_step": int(h_delta.numel() * 4 + h_acc.numel()),
                "d2h_bytes_per_step": int(h_out.numel() * 4)}
 
