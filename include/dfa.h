@@ -79,6 +79,15 @@ typedef enum dfa_algo {
 #define DFA_FLAG_TABLE_ONLY 0x2u   /* signature refinement: renumber through the exact hash table in
                                       every round (no direct or filter rounds); same results, for
                                       comparisons and tests */
+#define DFA_FLAG_STOP_DISCRETE 0x4u  /* signature refinement: stop after the round that leaves n
+                                      blocks.  A partition of singletons cannot split, so the
+                                      confirming round of Algorithm 4's until-test is not run and
+                                      rounds_executed == rounds_changed for such inputs.  This is
+                                      how Table 2's iteration counts for B_n (n - 1) come out.
+                                      Same partition as without the flag.  Honoured by
+                                      dfa_minimise, dfa_minimise_noalloc, dfa_minimise_batch and
+                                      dfa_equivalent; ignored by naivePR, transPR and the
+                                      server. */
 
 typedef struct dfa_opts {
   int32_t algo;            /* dfa_algo */
@@ -90,7 +99,8 @@ typedef struct dfa_opts {
 
 /* Round counts follow Algorithm 4's loop: rounds_changed counts rounds whose
  * block count grew; rounds_executed also counts the final round that finds the
- * count unchanged (the fixpoint test).  For naivePR/transPR a round is one
+ * count unchanged (the fixpoint test), unless DFA_FLAG_STOP_DISCRETE ended the
+ * loop at n blocks.  For naivePR/transPR a round is one
  * iteration of Algorithm 2's while-loop, the last one finding no split. */
 typedef struct dfa_result {
   uint32_t num_blocks;

@@ -181,11 +181,14 @@ def moore_round(delta: np.ndarray, block: np.ndarray) -> np.ndarray:
     return kernel_of(cols)
 
 
-def moore(delta, accept, max_rounds: int | None = None, history: bool = False) -> RefineResult:
+def moore(delta, accept, max_rounds: int | None = None, history: bool = False,
+          stop_discrete: bool = False) -> RefineResult:
     """Signature refinement until the number of blocks stops growing (Algorithm 4).
 
     The result is the coarsest partition of all n states that respects F and is a
-    congruence for δ (Nerode equivalence over Q)."""
+    congruence for δ (Nerode equivalence over Q).  With stop_discrete the loop also
+    ends after a round that leaves n blocks: singletons cannot split, so the
+    until-test's confirming round is skipped (Table 2 counts B_n this way)."""
     delta, accept = _prep(delta, accept)
     block = initial_partition(accept)
     count = int(block.max()) + 1
@@ -204,6 +207,8 @@ def moore(delta, accept, max_rounds: int | None = None, history: bool = False) -
             break
         changed += 1
         block, count = new, new_count
+        if stop_discrete and count == block.shape[0]:
+            break
     res = RefineResult(block, int(block.max()) + 1, changed, executed, counts)
     if history:
         res.history = hist
@@ -314,7 +319,8 @@ class EquivResult:
     separated_round: int      # round in which the two start states first differ, -1 if never
 
 
-def equivalent(dA, accA, sA, dB, accB, sB, early_exit: bool = False) -> EquivResult:
+def equivalent(dA, accA, sA, dB, accB, sB, early_exit: bool = False,
+               stop_discrete: bool = False) -> EquivResult:
     """L(A) = L(B) iff q0A and q0B end in the same block of the coarsest partition of
     A ⊎ B.  With early_exit, refinement stops at the first round whose partition
     separates the two start states (that round number is the length of a shortest
@@ -323,7 +329,7 @@ def equivalent(dA, accA, sA, dB, accB, sB, early_exit: bool = False) -> EquivRes
     nA = np.asarray(accA).shape[0]
     sBu = nA + int(sB)
     if not early_exit:
-        r = moore(d, acc, history=True)
+        r = moore(d, acc, history=True, stop_discrete=stop_discrete)
         sep = -1
         for i, h in enumerate(r.history):
             if h[sA] != h[sBu]:
@@ -348,6 +354,8 @@ def equivalent(dA, accA, sA, dB, accB, sB, early_exit: bool = False) -> EquivRes
         block, count = new, new_count
         if block[sA] != block[sBu]:
             return EquivResult(False, RefineResult(block, count, changed, executed, counts), executed)
+        if stop_discrete and count == block.shape[0]:
+            break
     return EquivResult(True, RefineResult(block, int(block.max()) + 1, changed, executed, counts), -1)
 
 

@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "DFA_OK", -1: "DFA_EINVAL", -2: "DFA_ENOMEM", -3: "DFA_ECUDA"
 ALGOS = {"moore": 0, "naive": 1, "trans": 2}
 DFA_FLAG_EARLY_EXIT = 0x1
 DFA_FLAG_TABLE_ONLY = 0x2
+DFA_FLAG_STOP_DISCRETE = 0x4
 DFA_REQ_MINIMISE, DFA_REQ_EQUIVALENT = 0, 1
 
 
@@ -255,11 +256,11 @@ def minimise(delta, accept, algo="moore", max_rounds=0, timeout_ns=0, out=None, 
     return out, res
 
 
-def equivalent(A, B, early_exit=False, timeout_ns=0, workspace=None, stream=None, check=True):
+def equivalent(A, B, early_exit=False, timeout_ns=0, workspace=None, stream=None, check=True, flags=0):
     """L(A) = L(B)?  A and B are (delta, accept, start) triples.  Returns (bool, DfaResult)."""
     a, ka = make_dfa(A[0], A[1], A[2])
     b, kb = make_dfa(B[0], B[1], B[2])
-    o = make_opts("moore", 0, timeout_ns, flags=DFA_FLAG_EARLY_EXIT if early_exit else 0)
+    o = make_opts("moore", 0, timeout_ns, flags=(DFA_FLAG_EARLY_EXIT if early_exit else 0) | int(flags))
     need = dfa_equivalent_workspace_size(a, b, o)
     if need == 0:
         raise DfaError(DFA_EINVAL, last_error() or "bad arguments")
@@ -273,14 +274,14 @@ def equivalent(A, B, early_exit=False, timeout_ns=0, workspace=None, stream=None
 
 
 def minimise_batch(dfas, algo="moore", max_rounds=0, timeout_ns=0, schedule=-1, out=None, workspace=None,
-                   stream=None, check=True):
+                   stream=None, check=True, flags=0):
     """Refine a list of (delta, accept) pairs in one launch.  Returns (blocks, [DfaResult])."""
     structs, keep = [], []
     for item in dfas:
         d, kk = make_dfa(item[0], item[1])
         structs.append(d)
         keep.append(kk)
-    o = make_opts(algo, max_rounds, timeout_ns, schedule)
+    o = make_opts(algo, max_rounds, timeout_ns, schedule, flags)
     total = sum(s.n for s in structs)
     if out is None:
         import torch

@@ -112,6 +112,7 @@ MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_ac
   L.tmp = take(n * 4);
   const size_t warps = moore_max_warps();
   L.dups = take((n + (warps + 2) * 32) * 4);   // n plus one partial chunk per warp
+  L.dups2 = take((n + (warps + 2) * 32) * 4);
   L.wcnt = take(warps * 4);
   L.minrep = take(S * 4);
   L.flag = take(n);
@@ -156,9 +157,11 @@ int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, 
   a.mbits = L.mbits;
   a.rep = reinterpret_cast<unsigned long long *>(ws + L.rep);
   a.dups = reinterpret_cast<uint32_t *>(ws + L.dups);
+  a.dups2 = reinterpret_cast<uint32_t *>(ws + L.dups2);
   a.wcnt = reinterpret_cast<uint32_t *>(ws + L.wcnt);
   a.wid = L.wid;
   a.modes = (o.flags & DFA_FLAG_TABLE_ONLY) ? 0u : 3u;
+  a.stop_discrete = (o.flags & DFA_FLAG_STOP_DISCRETE) ? 1u : 0u;
   a.flag = reinterpret_cast<uint8_t *>(ws + L.flag);
   a.partials = reinterpret_cast<uint32_t *>(ws + L.partials);
   a.out = out_dev;

@@ -14,7 +14,7 @@ namespace dfa {
 // (SIZE_MAX = absent).
 struct MooreLayout {
   uint32_t log2S, mbits, wid, ebits;
-  size_t ctrl, table, lab0, lab1, tmp, minrep, flag, partials, bm0, bm1, seen1, seen2, seen3, seen4, tmp2, rep, dups, wcnt, delta, accept, out,
+  size_t ctrl, table, lab0, lab1, tmp, minrep, flag, partials, bm0, bm1, seen1, seen2, seen3, seen4, tmp2, rep, dups, dups2, wcnt, delta, accept, out,
       total;
 };
 

@@ -73,6 +73,7 @@ struct BatchArgs {
   uint32_t *base;          // nsegs
   Ctrl *ctrl;
   uint32_t ebits, max_stages, max_rounds;
+  uint32_t stop_discrete;  // 1: a DFA whose round leaves n blocks stops (no confirming round)
   uint32_t vec;            // states per lane within a tile pass: 1 or 2
   unsigned long long timeout_ns, barrier_ns;
 };
@@ -241,7 +242,9 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs A) {
       } else {
         w[SS_CHANGED] += 1;
         w[SS_PREV] = B;
-        if (A.max_rounds != 0u && r >= A.max_rounds) {
+        if (A.stop_discrete && B == A.segs[i].n) {
+          w[SS_ACTIVE] = 0u;             // n singleton blocks cannot split any further
+        } else if (A.max_rounds != 0u && r >= A.max_rounds) {
           w[SS_ACTIVE] = 0u;
           w[SS_MAXED] = 1u;
         } else {
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs A) {
   }
   if (ok) {
     ok = canonicalise(CanonArgs{A.total_states, A.fin, (size_t)A.total_slots, A.minrep, A.flag, A.partials, A.out,
-                                C, A.barrier_ns},
+                                C, A.barrier_ns, 0u},
                       0xFFFFFFFFu, s_red);
   }
   if (ok) ok = grid_sync(C, A.barrier_ns);
@@ -537,6 +540,7 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const dfa_opts &o, uint3
   a.ebits = L.ebits;
   a.max_stages = L.max_stages;
   a.max_rounds = o.max_rounds;
+  a.stop_discrete = (o.flags & DFA_FLAG_STOP_DISCRETE) ? 1u : 0u;
   a.vec = vec;
   a.timeout_ns = o.timeout_ns;
   a.barrier_ns = o.timeout_ns < 5000000000ull ? o.timeout_ns : 5000000000ull;

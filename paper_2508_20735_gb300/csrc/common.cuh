@@ -36,7 +36,8 @@ struct Ctrl {
   uint32_t verdict;        // equivalence: 1 = same block
   uint32_t maxed;          // stopped at opts.max_rounds (not an error for the barrier)
   uint32_t qf, qn;         // naivePR: initial leaders (min F, min Q\F)
-  uint32_t ndup;           // filter rounds: states listed for the exact table
+  uint32_t ndup;           // filter rounds: states listed by the first filter
+  uint32_t nstill;         // filter rounds: listed states left for the exact table
   unsigned long long t_start, t_end;
   unsigned long long deadline;  // absolute %globaltimer value
 };
@@ -108,6 +109,11 @@ __device__ __forceinline__ unsigned long long policy_evict_last() {
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
+__device__ __forceinline__ unsigned long long policy_evict_normal() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ unsigned long long policy_evict_first() {
   unsigned long long p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -134,6 +140,14 @@ __device__ __forceinline__ void st_v4_hint(uint32_t *p, uint4 v, unsigned long l
   asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
                "r"(v.w), "l"(pol)
                : "memory");
+}
+__device__ __forceinline__ uint32_t atom_or_hint(uint32_t *p, uint32_t v, unsigned long long pol) {
+  uint32_t old;
+  asm volatile("atom.global.L2::cache_hint.or.b32 %0, [%1], %2, %3;" : "=r"(old) : "l"(p), "r"(v), "l"(pol) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_or_hint(uint32_t *p, uint32_t v, unsigned long long pol) {
+  asm volatile("red.global.L2::cache_hint.or.b32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
 }
 __device__ __forceinline__ void st_u32_hint(uint32_t *p, uint32_t v, unsigned long long pol) {
   asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
@@ -433,6 +447,7 @@ struct CanonArgs {
   uint32_t *out;           // n
   Ctrl *ctrl;
   unsigned long long barrier_ns;
+  uint32_t min_labels;     // 1: every label already is its block's smallest state
 };
 
 // Canonical numbering of the final labels: block id = rank of its smallest
@@ -449,22 +464,24 @@ static __device__ __noinline__ bool canonicalise(const CanonArgs &A, uint32_t B,
     return true;
   }
   const size_t S = A.label_space;
-  for (size_t i = tid; i < S; i += stride) A.minrep[i] = 0xFFFFFFFFu;
-  if (!grid_sync(C, A.barrier_ns)) return false;
-  {
-    // lanes hold consecutive states, so the lowest lane of a label group holds
-    // the group's smallest state: one atomic per (warp, label)
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t gwarp = tid >> 5, nwarps = stride >> 5;
-    for (uint64_t base = (uint64_t)gwarp * 32; base < n; base += (uint64_t)nwarps * 32) {
-      const uint32_t q = (uint32_t)base + lane;
-      const bool valid = q < n;
-      const uint32_t l = valid ? lab[q] : 0u;
-      const unsigned grp = __match_any_sync(0xFFFFFFFFu, l) & __ballot_sync(0xFFFFFFFFu, valid);
-      if (valid && lane == (uint32_t)(__ffs(grp) - 1)) atomicMin(&A.minrep[l], q);
+  if (!A.min_labels) {   // smallest member per label
+    for (size_t i = tid; i < S; i += stride) A.minrep[i] = 0xFFFFFFFFu;
+    if (!grid_sync(C, A.barrier_ns)) return false;
+    {
+      // lanes hold consecutive states, so the lowest lane of a label group holds
+      // the group's smallest state: one atomic per (warp, label)
+      const uint32_t lane = threadIdx.x & 31u;
+      const uint32_t gwarp = tid >> 5, nwarps = stride >> 5;
+      for (uint64_t base = (uint64_t)gwarp * 32; base < n; base += (uint64_t)nwarps * 32) {
+        const uint32_t q = (uint32_t)base + lane;
+        const bool valid = q < n;
+        const uint32_t l = valid ? lab[q] : 0u;
+        const unsigned grp = __match_any_sync(0xFFFFFFFFu, l) & __ballot_sync(0xFFFFFFFFu, valid);
+        if (valid && lane == (uint32_t)(__ffs(grp) - 1)) atomicMin(&A.minrep[l], q);
+      }
     }
+    if (!grid_sync(C, A.barrier_ns)) return false;
   }
-  if (!grid_sync(C, A.barrier_ns)) return false;
   // contiguous chunk per block, a multiple of blockDim
   uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
   chunk = (chunk + blockDim.x - 1) / blockDim.x * blockDim.x;
@@ -473,7 +490,7 @@ static __device__ __noinline__ bool canonicalise(const CanonArgs &A, uint32_t B,
   const uint32_t end = (uint64_t)beg + chunk < n ? beg + chunk : n;
   uint32_t cnt = 0;
   for (uint32_t q = beg + threadIdx.x; q < end; q += blockDim.x) {
-    const uint8_t f = A.minrep[lab[q]] == q;
+    const uint8_t f = A.min_labels ? (lab[q] == q) : (A.minrep[lab[q]] == q);
     A.flag[q] = f;
     cnt += f;
   }

@@ -44,6 +44,7 @@ struct MooreArgs {
   uint32_t mbits;
   unsigned long long *rep; // 2^log2S: filter-mode smallest member per table slot
   uint32_t *dups;          // filter-mode per-warp lists of states in shared buckets
+  uint32_t *dups2;         // second-filter bucket of each listed state (same positions)
   uint32_t *wcnt;          // per-warp list lengths
   uint32_t wid;            // bits of a state number (labels of filter rounds)
   uint8_t *flag;           // n: canonicalisation scratch
@@ -61,6 +62,7 @@ struct MooreArgs {
   uint32_t sep_a, sep_b;
   uint32_t track_pair;     // 1: record the round separating sep_a and sep_b
   uint32_t early_exit;
+  uint32_t stop_discrete;  // 1: stop after a round that leaves n blocks (no confirming round)
 };
 
 struct LaunchInfo {

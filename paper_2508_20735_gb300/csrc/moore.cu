@@ -194,12 +194,16 @@ __device__ __forceinline__ void clear_table(u128 *table, uint32_t log2S) {
 // signatures tells whether a signature is new (the first atomicOr to set its
 // bit counts one block).  Signatures of at most 13 bits are first collected in
 // a per-block bitmap in shared memory and merged once per block.
+// Direct rounds with keys of at most kSmallK bits mark them in a shared-memory
+// bitmap first; wider keys go straight to the global bitmap.
+static constexpr uint32_t kSmallK = 13;
+
 template <bool ROUND1>
 __device__ __forceinline__ void direct_pass(const MooreArgs &A, uint32_t w, uint32_t K, const uint32_t *__restrict__ src,
                                             uint32_t *__restrict__ dst, uint32_t *bm, uint32_t &local_new,
                                             uint32_t &seen, uint32_t *sbm) {
   const uint32_t n = A.n, k = A.k;
-  const bool small = K <= 13;
+  const bool small = K <= kSmallK;
   const uint32_t swords = small ? ((1u << K) + 31) / 32 : 0;
   if (small) {
     for (uint32_t i = threadIdx.x; i < swords; i += blockDim.x) sbm[i] = 0u;
@@ -236,12 +240,8 @@ __device__ __forceinline__ void direct_pass(const MooreArgs &A, uint32_t w, uint
     const unsigned grp = __match_any_sync(0xFFFFFFFFu, valid ? key : 0xFFFFFFFFu) & vm;
     if (valid && lane == (uint32_t)(__ffs(grp) - 1)) {
       const uint32_t bit = 1u << (key & 31u);
-      if (small) {
-        atomicOr(&sbm[key >> 5], bit);
-      } else {
-        const uint32_t old = atomicOr(&bm[key >> 5], bit);
-        if (!(old & bit)) ++local_new;
-      }
+      if (small) atomicOr(&sbm[key >> 5], bit);
+      else red_or_hint(&bm[key >> 5], bit, keep);   // counted by popcount after the pass
     }
   }
   if (small) {
@@ -306,49 +306,81 @@ __device__ __forceinline__ void filter_pass_a(const MooreArgs &A, const uint32_t
     h ^= h >> 33;
     const uint32_t b = (uint32_t)(h >> (64 - A.mbits));
     const uint32_t bit = 1u << (b & 31u);
-    const uint32_t old = atomicOr(&A.seen1[b >> 5], bit);
-    if (old & bit) atomicOr(&A.seen2[b >> 5], bit);
-    A.tmp[q] = b;
+    // counters stay in L2 beside the labels; the buckets are streamed out
+    const uint32_t old = atom_or_hint(&A.seen1[b >> 5], bit, keep);
+    if (old & bit) red_or_hint(&A.seen2[b >> 5], bit, keep);
+    st_u32_hint(A.tmp + q, b, drop);
     // an independent bucket for the second filter (states listed by pass B)
     unsigned long long h2 = (h ^ 0x9E3779B97F4A7C15ull) * 0xc4ceb9fe1a85ec53ull;
     h2 ^= h2 >> 31;
-    A.tmp2[q] = (uint32_t)(h2 >> (64 - (A.mbits - 1)));
+    st_u32_hint(A.tmp2 + q, (uint32_t)(h2 >> (64 - (A.mbits - 1))), drop);
   }
 }
 
 // The listed states of a filter round live in per-warp slices of `dups`: warp
 // g owns [g*cap, g*cap + count_g), cap = ceil(states per warp / 32) * 32, and
-// appends with a register cursor (no global atomics).  Passes D and C walk the
-// same slices with the same warps.
+// appends with a register cursor (no global atomics).  `dups2` holds, at the
+// same positions, each listed state's bucket in the second filter.  Passes G
+// and C walk the same slices with the same warps.
 __device__ __forceinline__ uint32_t dup_cap(uint32_t n, uint32_t nwarps) {
   const uint32_t chunks = (n + 31) / 32;
   return (chunks + nwarps - 1) / nwarps * 32;
 }
 
 // Pass B: a signature alone in its bucket is unique: its state becomes a
-// singleton block labelled with its own number.  The others are listed.
+// singleton block labelled with its own number.  The others are listed and
+// enter a second filter with an independent bucket of A.mbits - 1 bits (most
+// listed signatures merely collided with another one in the first filter).
+// Each warp takes its chunks (c = warp, warp + nwarps, ...) kB at a time, so
+// that the loads of kB chunks are in flight together.
+static constexpr int kB = 4;
 __device__ __forceinline__ void filter_pass_b(const MooreArgs &A, uint32_t *__restrict__ dst, uint32_t &local_new) {
   const uint32_t n = A.n;
   const unsigned long long drop = policy_evict_first();
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-  uint32_t *list = A.dups + (size_t)gwarp * dup_cap(n, nwarps);
+  const uint32_t chunks = (n + 31) / 32;
+  const size_t at = (size_t)gwarp * dup_cap(n, nwarps);
+  uint32_t *list = A.dups + at, *list2 = A.dups2 + at;
   uint32_t cursor = 0;
-  for (uint64_t base = (uint64_t)gwarp * 32; base < n; base += (uint64_t)nwarps * 32) {
-    const uint32_t q = (uint32_t)base + lane;
-    const bool valid = q < n;
-    bool dup = false;
-    if (valid) {
-      const uint32_t b = A.tmp[q];
-      dup = (A.seen2[b >> 5] >> (b & 31u)) & 1u;
-      if (!dup) {
-        st_u32_hint(dst + q, q, drop);
+  for (uint64_t c0 = gwarp; c0 < chunks; c0 += (uint64_t)kB * nwarps) {
+    uint32_t q[kB], b[kB], wd[kB], b2[kB];
+    bool valid[kB], dup[kB];
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const uint64_t qq = (c0 + (uint64_t)j * nwarps) * 32 + lane;
+      valid[j] = qq < n;
+      q[j] = valid[j] ? (uint32_t)qq : 0u;
+      b[j] = valid[j] ? ld_u32_stream(A.tmp + q[j], drop) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kB; ++j) wd[j] = valid[j] ? A.seen2[b[j] >> 5] : 0u;
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      dup[j] = valid[j] && ((wd[j] >> (b[j] & 31u)) & 1u);
+      b2[j] = dup[j] ? ld_u32_stream(A.tmp2 + q[j], drop) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      if (dup[j]) {
+        const uint32_t bit = 1u << (b2[j] & 31u);
+        const uint32_t old = atomicOr(&A.seen3[b2[j] >> 5], bit);
+        if (old & bit) atomicOr(&A.seen4[b2[j] >> 5], bit);
+      } else if (valid[j]) {
+        st_u32_hint(dst + q[j], q[j], drop);
         ++local_new;
       }
     }
-    const unsigned dm = __ballot_sync(0xFFFFFFFFu, dup);
-    if (dup) list[cursor + __popc(dm & ((1u << lane) - 1u))] = q;
-    cursor += __popc(dm);
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const unsigned dm = __ballot_sync(0xFFFFFFFFu, dup[j]);
+      if (dup[j]) {
+        const uint32_t p = cursor + __popc(dm & ((1u << lane) - 1u));
+        list[p] = q[j];
+        list2[p] = b2[j];
+      }
+      cursor += __popc(dm);
+    }
   }
   if (lane == 0) {
     A.wcnt[gwarp] = cursor;
@@ -356,60 +388,62 @@ __device__ __forceinline__ void filter_pass_b(const MooreArgs &A, uint32_t *__re
   }
 }
 
-// Passes E and F: a second filter over the listed states only, with an
-// independent bucket of A.mbits - 1 bits.  Most listed signatures merely
-// collided with another one in the first filter; alone in their second bucket
-// they are unique too (pass F labels them with their state number and keeps
-// the rest listed, compacted in place within the warp's slice).
-__device__ __forceinline__ void filter_pass_e(const MooreArgs &A) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t *list = A.dups + (size_t)gwarp * dup_cap(A.n, nwarps);
-  const uint32_t nd = A.wcnt[gwarp];
-  for (uint32_t i = lane; i < nd; i += 32) {
-    const uint32_t b = A.tmp2[list[i]];
-    const uint32_t bit = 1u << (b & 31u);
-    const uint32_t old = atomicOr(&A.seen3[b >> 5], bit);
-    if (old & bit) atomicOr(&A.seen4[b >> 5], bit);
-  }
-}
-
+// Pass F: a listed state alone in its second bucket is unique too: it is
+// labelled with its own number.  The rest stay listed, compacted in place
+// within the warp's slice, and are counted in ctrl->nstill.
 __device__ __forceinline__ void filter_pass_f(const MooreArgs &A, uint32_t *__restrict__ dst, uint32_t &local_new) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-  uint32_t *list = A.dups + (size_t)gwarp * dup_cap(A.n, nwarps);
+  const size_t at = (size_t)gwarp * dup_cap(A.n, nwarps);
+  uint32_t *list = A.dups + at;
+  const uint32_t *list2 = A.dups2 + at;
   const uint32_t nd = A.wcnt[gwarp];
   uint32_t cursor = 0;
   for (uint32_t base = 0; base < nd; base += 32) {
     const uint32_t i = base + lane;
     const bool valid = i < nd;
-    bool still = false;
     uint32_t q = 0;
+    bool still = false;
     if (valid) {
       q = list[i];
-      const uint32_t b = A.tmp2[q];
-      still = (A.seen4[b >> 5] >> (b & 31u)) & 1u;
+      const uint32_t b2 = list2[i];
+      still = (A.seen4[b2 >> 5] >> (b2 & 31u)) & 1u;
       if (!still) {
         dst[q] = q;
         ++local_new;
       }
     }
-    // every lane has read its entry before any lane writes (positions <= reads)
+    // every lane read its entry above (q feeds the ballot): positions <= reads
     const unsigned sm = __ballot_sync(0xFFFFFFFFu, still);
     if (still) list[cursor + __popc(sm & ((1u << lane) - 1u))] = q;
     cursor += __popc(sm);
   }
   __syncwarp();
-  if (lane == 0) A.wcnt[gwarp] = cursor;
+  if (lane == 0) {
+    A.wcnt[gwarp] = cursor;
+    if (cursor) atomicAdd(&A.ctrl->nstill, cursor);
+  }
 }
 
-// Pass D: the listed states insert their exact keys; each slot keeps its
-// smallest member via atomicMax on (round << 32 | ~state), one atomic per
-// (warp, slot).
+// Table size (log2 slots) of a filter round's exact insert: at least twice
+// the listed states left (so that the region to clear stays small), at least
+// 2^10 slots, never more than the table's 2^log2S.
+__device__ __forceinline__ uint32_t filter_table_bits(uint32_t nstill, uint32_t log2S) {
+  uint32_t m = log2S < 10 ? log2S : 10;
+  while (m < log2S && ((uint64_t)1 << m) < 2ull * nstill) ++m;
+  return m;
+}
+
+// Keys of filter rounds carry this tag; their region is cleared every round.
+static constexpr uint32_t kFilterTag = 1;
+
+// Pass D: the listed states left insert their exact keys into the region of
+// 2^m slots cleared for this round; each slot keeps its smallest member via
+// atomicMax on (round << 32 | ~state), one atomic per (warp, slot).
 __device__ __forceinline__ void filter_pass_d(const MooreArgs &A, uint32_t w, const uint32_t *__restrict__ src,
-                                              uint32_t epoch, uint32_t r, CtaCache *cache) {
+                                              uint32_t m, uint32_t r, CtaCache *cache) {
   const unsigned long long keep = policy_evict_last(), drop = policy_evict_first();
-  const unsigned long long etag = (unsigned long long)epoch << (64 - A.ebits);
+  const unsigned long long etag = (unsigned long long)kFilterTag << (64 - A.ebits);
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t *list = A.dups + (size_t)gwarp * dup_cap(A.n, nwarps);
@@ -423,7 +457,7 @@ __device__ __forceinline__ void filter_pass_d(const MooreArgs &A, uint32_t w, co
     key[0].hi |= etag;
     uint32_t slot[1];
     uint32_t created = 0;
-    warp_insert<1>(A.table, A.log2S, key, valid, A.ebits, epoch, slot, created, &A.ctrl->err, cache);
+    warp_insert<1>(A.table, m, key, valid, A.ebits, kFilterTag, slot, created, &A.ctrl->err, cache);
     if (valid) A.tmp[q] = slot[0];
     // listed states are ascending within the slice, so the lowest lane of a
     // slot group holds the group's smallest state
@@ -465,7 +499,7 @@ template <int VEC>
 __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
   __shared__ uint32_t s_red[kThreads / 32];
   __shared__ CtaCache cache;
-  __shared__ uint32_t sbm[(1u << 13) / 32];
+  __shared__ uint32_t sbm[(1u << kSmallK) / 32];
   Ctrl *C = A.ctrl;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
@@ -480,6 +514,7 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
   uint32_t epoch = 0, r = 0, changed = 0, B_prev = 0, final_buf = 0, B_final = 0xFFFFFFFFu;
   uint32_t w = 1;              // bits of the labels the next round reads (round 0: acceptance bits)
   uint32_t final_space = 2;    // label space of the final labels
+  bool final_min = false;      // final labels are smallest members (filter rounds)
   bool ok = true, separated = false, skip = false, table_clean = false;
   bool filter_ok = true;       // cleared for good once a filter round lists most states
 
@@ -512,9 +547,8 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
     uint32_t mode = MODE_TABLE;
     if ((A.modes & 1u) && K <= A.log2S && K <= 27) mode = MODE_DIRECT;
     else if ((A.modes & 2u) && filter_ok && !round1 && K <= 125 && (uint64_t)B_prev * 64 >= A.n) mode = MODE_FILTER;
-    if (mode != MODE_DIRECT && !table_clean) {   // first table round: the table and slot owners start clean
+    if (mode == MODE_TABLE && !table_clean) {   // first table round: the table starts clean
       clear_table(A.table, A.log2S);
-      for (size_t i = tid; i < S; i += stride) A.rep[i] = 0ull;
       ok = grid_sync(C, A.barrier_ns);
       if (!ok) break;
       table_clean = true;
@@ -525,16 +559,16 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
     if (mode == MODE_DIRECT) {
       if (round1) direct_pass<true>(A, w, (uint32_t)K, src, dst, A.bm[r & 1], local_new, seen, sbm);
       else direct_pass<false>(A, w, (uint32_t)K, src, dst, A.bm[r & 1], local_new, seen, sbm);
+      if (K > kSmallK) {   // labels marked without return values: count the bitmap
+        ok = grid_sync(C, A.barrier_ns);
+        if (!ok) break;
+        const uint32_t words = (uint32_t)(((1ull << K) + 31) / 32);
+        for (uint32_t i = tid; i < words; i += stride) local_new += __popc(__ldcg(A.bm[r & 1] + i));
+      }
       w = (uint32_t)K;
       final_space = 1u << K;
+      final_min = false;
     } else if (mode == MODE_FILTER) {
-      if (epoch == emax) {
-        clear_table(A.table, A.log2S);
-        ok = grid_sync(C, A.barrier_ns);
-        epoch = 0;
-        if (!ok) break;
-      }
-      ++epoch;
       filter_pass_a(A, src);
       ok = grid_sync(C, A.barrier_ns);
       if (!ok) break;
@@ -543,19 +577,24 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
       if (!ok) break;
       // mostly true duplicates (large blocks): later rounds use the table path
       if ((uint64_t)ld_relaxed(&C->ndup) * 2 > A.n) filter_ok = false;
-      filter_pass_e(A);
-      ok = grid_sync(C, A.barrier_ns);
-      if (!ok) break;
       filter_pass_f(A, dst, local_new);
       ok = grid_sync(C, A.barrier_ns);
       if (!ok) break;
+      const uint32_t m = filter_table_bits(ld_relaxed(&C->nstill), A.log2S);
+      clear_table(A.table, m);
+      for (size_t i = tid; i < ((size_t)1 << m); i += stride) A.rep[i] = 0ull;
+      // the region now holds filter-tagged keys: a later table round starts from a full clear
+      table_clean = false;
+      ok = grid_sync(C, A.barrier_ns);
+      if (!ok) break;
       cta_cache_clear(&cache);
-      filter_pass_d(A, w, src, epoch, r, &cache);
+      filter_pass_d(A, w, src, m, r, &cache);
       ok = grid_sync(C, A.barrier_ns);
       if (!ok) break;
       filter_pass_c(A, dst, local_new);
       w = A.wid;
       final_space = A.n;
+      final_min = true;
     } else {
       const StagePlan P = make_plan(A.k, w, A.log2S);
       for (uint32_t s = 0; s < P.stages && ok; ++s) {
@@ -574,6 +613,7 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
       if (!ok) break;
       w = A.log2S;
       final_space = (uint32_t)S;
+      final_min = false;
     }
     const uint32_t bnew = block_sum(local_new, s_red);
     if (threadIdx.x == 0 && bnew) atomicAdd(&C->cnt[r % 3], bnew);
@@ -590,7 +630,8 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
     if (round1) B_prev = (ld_relaxed(&C->seen_acc) != 0u) + (ld_relaxed(&C->seen_rej) != 0u);
     if (leader) {
       C->cnt[(r + 2) % 3] = 0u;
-      C->ndup = 0u;   // read only inside a filter round, after its pass B
+      C->ndup = 0u;     // read only inside a filter round, after its pass B
+      C->nstill = 0u;   // read only inside a filter round, after its pass F
     }
     final_buf = r & 1;
     B_final = B_r;
@@ -605,6 +646,7 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
       }
     }
     if (!grew) break;   // fixpoint: the round did not add a block (Algorithm 4's until-test)
+    if (A.stop_discrete && B_r == A.n) break;   // n singleton blocks cannot split any further
     if (A.max_rounds != 0u && r >= A.max_rounds) {
       if (leader) C->maxed = 1u;
       break;
@@ -619,7 +661,7 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
     }
     const size_t space = skip ? 2 : final_space;
     ok = canonicalise(CanonArgs{A.n, A.lab[final_buf], space < S ? space : S, A.minrep, A.flag, A.partials, A.out,
-                                A.ctrl, A.barrier_ns},
+                                A.ctrl, A.barrier_ns, final_min ? 1u : 0u},
                       B_final, s_red);
   }
   if (leader) C->t_end = gtimer();

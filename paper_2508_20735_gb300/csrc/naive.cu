@@ -173,8 +173,9 @@ __global__ void __launch_bounds__(kNaiveThreads) naive_kernel(NaiveArgs A) {
       C->rounds_executed = r;
       C->rounds_changed = changed;
     }
+    // leaders are the smallest members of their blocks (Algorithm 2 with min-leader election)
     ok = canonicalise(CanonArgs{n, A.blk[final_buf], (size_t)n, A.minrep, A.flag, A.partials, A.out, C,
-                                A.barrier_ns},
+                                A.barrier_ns, 1u},
                       0xFFFFFFFFu, s_red);
   }
   if (leader) C->t_end = gtimer();

@@ -540,7 +540,7 @@ static void worker_main(dfa_server *s) {
         CanonArgs ca{r.n, reinterpret_cast<uint32_t *>(b + (r.round & 1 ? r.o_lab1 : r.o_lab0)),
                      (size_t)1 << r.log2S, reinterpret_cast<uint32_t *>(b + r.o_minrep),
                      reinterpret_cast<uint8_t *>(b + r.o_flag), partials, reinterpret_cast<uint32_t *>(b + r.o_out),
-                     ctrl, 5000000000ull};
+                     ctrl, 5000000000ull, 0u};
         uint32_t B = r.lastB;
         cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s->stream);
         void *cp[] = {&ca, &B};

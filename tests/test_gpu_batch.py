@@ -61,6 +61,17 @@ def test_mixed_batch_against_oracle(g, schedule):
             (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
 
 
+@pytest.mark.parametrize("schedule", [0, -1])
+def test_mixed_batch_stop_discrete(g, schedule):
+    dfas = _mixed()
+    blocks, res = _batch(g, dfas, schedule=schedule, flags=g.DFA_FLAG_STOP_DISCRETE)
+    for A, b, r in zip(dfas, blocks, res):
+        ref = oracle.moore(A.delta, A.accept, stop_discrete=True)
+        assert np.array_equal(b, ref.block)
+        assert (r.num_blocks, r.rounds_changed, r.rounds_executed) == \
+            (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
+
+
 def test_batch_equals_alone_and_host_inputs(g):
     dfas = _mixed()[:10]
     blocks, res = _batch(g, dfas, host=True)

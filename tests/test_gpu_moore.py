@@ -159,6 +159,37 @@ def test_bench_workload_2p24(g):
     _assert_parity(g, A)
 
 
+# ---------------------------------------------------------------- stopping at n blocks
+
+def _stop_cases():
+    return [dfagen.random_dfa(10_000, 2, 0.5, 1), dfagen.random_dfa(300_000, 4, 0.5, 2),
+            dfagen.random_dfa(1, 2, 0.5, 4), dfagen.random_dfa(2, 1, 0.5, 5), dfagen.random_dfa(5000, 0, 0.5, 6),
+            dfagen.fibonacci_dfa(12), dfagen.bit_splitter(12), dfagen.chain_dfa(4096),
+            dfagen.planted_redundancy(dfagen.random_dfa(300, 3, 0.5, 61), 5, 2)[0],
+            dfagen.random_dfa(3000, 40, 0.5, 7), dfagen.random_dfa(65_537, 3, 0.3, 8)]
+
+
+@pytest.mark.parametrize("table_only", [False, True])
+@pytest.mark.parametrize("idx", range(11))
+def test_stop_discrete(g, idx, table_only):
+    A = _stop_cases()[idx]
+    ref = oracle.moore(A.delta, A.accept, stop_discrete=True)
+    flags = g.DFA_FLAG_STOP_DISCRETE | (g.DFA_FLAG_TABLE_ONLY if table_only else 0)
+    _assert_parity(g, A, ref=ref, flags=flags)
+
+
+def test_stop_discrete_bench_workload_2p24(g):
+    """The 2^24-state workload ends discrete: stopping at n blocks gives the
+    identity partition one round earlier than the plain loop (itself checked in
+    full against the oracle above)."""
+    A = dfagen.random_dfa(1 << 24, 4, 0.5, 2)
+    plain, rp = _gpu_moore(g, A)
+    got, rs = _gpu_moore(g, A, flags=g.DFA_FLAG_STOP_DISCRETE)
+    assert rp.num_blocks == A.n and rs.num_blocks == A.n
+    assert np.array_equal(got, np.arange(A.n, dtype=np.uint32))
+    assert rs.rounds_changed == rp.rounds_changed == rs.rounds_executed == rp.rounds_executed - 1
+
+
 # ---------------------------------------------------------------- errors
 
 def test_bad_transition_target(g):
@@ -214,6 +245,18 @@ def test_equivalence_pairs(g, req):
     if not expect:
         cex = oracle.shortest_cex(A.delta, A.accept, A.start, B.delta, B.accept, B.start)
         assert res2.rounds_executed == cex
+
+
+@pytest.mark.parametrize("req", range(6))
+def test_equivalence_stop_discrete(g, req):
+    A, B, expect = dfagen.equivalence_pair(100 + req, 5, n_lo=1000, n_hi=60_000)
+    args = (A.delta, A.accept, A.start, B.delta, B.accept, B.start)
+    for early in (False, True):
+        eq, res = g.equivalent(args[:3], args[3:], early_exit=early, flags=g.DFA_FLAG_STOP_DISCRETE)
+        ref = oracle.equivalent(*args, early_exit=early, stop_discrete=True)
+        assert eq == expect == ref.equivalent
+        assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
+            (ref.refine.num_blocks, ref.refine.rounds_changed, ref.refine.rounds_executed)
 
 
 def test_equivalence_start_acceptance_differs(g):

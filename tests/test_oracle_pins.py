@@ -111,6 +111,60 @@ def test_table_concur_bit_splitter_rows(name):
     assert r.counts[:-1] == [2 ** (i + 1) for i in range(m_)]
     nv = oracle.naive_pr(B.delta, B.accept)
     assert nv.rounds_changed == int(row["naive"]) and nv.num_blocks == row["size"]
+    # stopping at n singleton blocks reproduces the printed count as the number
+    # of rounds run, with the same partition
+    rd = oracle.moore(B.delta, B.accept, stop_discrete=True)
+    assert rd.rounds_executed == int(row["sort"]) == rd.rounds_changed
+    assert np.array_equal(rd.block, r.block)
+
+
+def _stop_discrete_cases():
+    yield dfagen.random_dfa(10_000, 2, 0.5, 1)
+    yield dfagen.random_dfa(3000, 4, 0.5, 2)
+    yield dfagen.random_dfa(2000, 2, 0.0, 3)          # one block
+    yield dfagen.random_dfa(1, 2, 0.5, 4)
+    yield dfagen.random_dfa(2, 1, 0.5, 5)
+    yield dfagen.fibonacci_dfa(9)
+    yield dfagen.bit_splitter(6)
+    yield dfagen.chain_dfa(64)
+    yield dfagen.cycle_dfa(10)
+    yield dfagen.planted_redundancy(dfagen.random_dfa(300, 3, 0.5, 61), 5, 2)[0]
+
+
+@pytest.mark.parametrize("idx", range(10))
+def test_stop_discrete_invariants(idx):
+    """Stopping at n blocks changes nothing but the confirming round: same
+    partition and block-count history; one round fewer exactly when the final
+    partition is discrete (and was reached by a growing round)."""
+    A = list(_stop_discrete_cases())[idx]
+    plain = oracle.moore(A.delta, A.accept)
+    fast = oracle.moore(A.delta, A.accept, stop_discrete=True)
+    assert np.array_equal(fast.block, plain.block)
+    assert fast.rounds_changed == plain.rounds_changed
+    assert fast.counts == plain.counts[:len(fast.counts)]
+    if plain.num_blocks == A.n and plain.rounds_changed > 0:
+        assert fast.rounds_executed == plain.rounds_executed - 1 == fast.rounds_changed
+        assert fast.counts[-1] == A.n
+    else:
+        assert fast.rounds_executed == plain.rounds_executed
+
+
+def test_stop_discrete_fib_row():
+    """Fib_N ends discrete, so stopping at n blocks runs N-2 rounds where
+    Table 2 prints N-1: the table counts Fib with the confirming round."""
+    A = dfagen.fibonacci_dfa(10)
+    r = oracle.moore(A.delta, A.accept, stop_discrete=True)
+    assert r.num_blocks == A.n and r.rounds_executed == r.rounds_changed == A.n - 2
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_stop_discrete_equivalence(seed):
+    """The verdict does not depend on stopping at n blocks (Hopcroft-Karp decides)."""
+    A, B, _ = dfagen.equivalence_pair(seed, 7, n_lo=20, n_hi=200)
+    args = (A.delta, A.accept, A.start, B.delta, B.accept, B.start)
+    expect = oracle.hk_equivalent(*args)
+    for early in (False, True):
+        assert oracle.equivalent(*args, early_exit=early, stop_discrete=True).equivalent == expect
 
 
 @pytest.mark.parametrize("i", range(3, 14))
