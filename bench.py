@@ -44,7 +44,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the CPU-oracle leg (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads (batch, chain, serve)")
-    return ap.parse_args()
+    ap.add_argument("--lg", type=int, default=24,
+                    help="profiling cases: 2^lg states instead of 2^24 (same k, seed and acceptance)")
+    ap.add_argument("--stop-discrete", action="store_true",
+                    help="profiling cases: time the call with DFA_FLAG_STOP_DISCRETE")
+    args = ap.parse_args()
+    if args.lg != 24:
+        WORKLOAD.update(workload=f"random_dfa_n2^{args.lg}_k4", n=1 << args.lg)
+    return args
 
 
 def dist_env():
@@ -288,7 +295,7 @@ def main():
     d_acc = torch.from_numpy(A.accept).cuda()
     out = torch.empty(n, dtype=torch.int32, device="cuda")
     dd, keep = g.make_dfa(d_delta, d_acc)
-    opts = g.make_opts("moore")
+    opts = g.make_opts("moore", flags=g.DFA_FLAG_STOP_DISCRETE if args.stop_discrete else 0)
     ws_bytes = g.dfa_workspace_size(dd, opts)
     ws = g._workspace(ws_bytes)
     stream = torch.cuda.current_stream()
@@ -337,7 +344,7 @@ def main():
                 "traffic": None, "kernel": "dfa::moore_kernel",
                 "algorithmic_bytes_per_launch": algo_bytes, "kernel_ms": kernel_s * 1e3}
     prof = os.path.join(ROOT, "profiles", "moore_kernel_traffic_random_n2p24_k4.txt")
-    if os.path.exists(prof):
+    if os.path.exists(prof) and args.lg == 24 and not args.stop_discrete:
         fields = {}
         with open(prof) as f:
             for line in f:
@@ -347,6 +354,22 @@ def main():
         # the figure is null once the kernel sources have changed since it was measured
         if fields.get("kernel_source_hash") == kernel_source_hash():
             roofline["traffic"] = int(fields["dram_bytes_per_launch"])
+
+    # the same workload stopping at n blocks (DFA_FLAG_STOP_DISCRETE): same partition, no confirming round
+    stop_discrete = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        sopts = g.make_opts("moore", flags=g.DFA_FLAG_STOP_DISCRETE)
+        sdev = []
+        for i in range(args.warmup + args.steps):
+            st, sr = g.dfa_minimise(dd, sopts, out.data_ptr(), ws.data_ptr(), ws_bytes, sptr)
+            if st != 0:
+                raise RuntimeError(f"dfa_minimise (stop at n blocks) failed: {st} {g.last_error()}")
+            if i >= args.warmup:
+                sdev.append(sr.device_ns)
+        sd_s = statistics.median(sdev) * 1e-9
+        stop_discrete = {"device_ms": sd_s * 1e3, "rounds": sr.rounds_executed, "blocks": sr.num_blocks,
+                         "transitions_per_s": n * k * sr.rounds_executed / sd_s,
+                         "plain_device_ms": statistics.median(dev_ns) * 1e-6}
 
     # end to end through the same C call with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -385,12 +408,14 @@ def main():
         del ws
         torch.cuda.empty_cache()
         ex = extras(g)
+        ex["random_n2p24_k4_stop_discrete"] = stop_discrete
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": dict(WORKLOAD, algo="moore (signature refinement)", rounds=rounds[-1],
+                               **({"flags": "DFA_FLAG_STOP_DISCRETE"} if args.stop_discrete else {}),
                                l2="inputs larger than L2 (delta 256 MiB)",
                                parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps,
