@@ -85,7 +85,7 @@ typedef enum dfa_algo {
                                       rounds_executed == rounds_changed for such inputs.  This is
                                       how Table 2's iteration counts for B_n (n - 1) come out.
                                       Same partition as without the flag.  Honoured by
-                                      dfa_minimise, dfa_minimise_noalloc, dfa_minimise_batch and
+                                      dfa_minimise, dfa_minimise_noalloc, both batch calls and
                                       dfa_equivalent; ignored by naivePR, transPR and the
                                       server. */
 
@@ -134,6 +134,26 @@ size_t dfa_batch_workspace_size(const dfa_t *dfas, uint32_t count, const dfa_opt
  * The DFAs' arrays may live anywhere (host or device), independently. */
 int dfa_minimise_batch(const dfa_t *dfas, uint32_t count, const dfa_opts *opts, uint32_t *block_out,
                        dfa_result *res, void *workspace, size_t ws_bytes, void *stream);
+
+/* The same batch given as two packed buffers instead of one dfa_t per DFA
+ * (the segment-offset form, no counterpart in the paper):
+ *   n, k     host arrays of `count` entries: DFA i has n[i] >= 1 states and
+ *            k[i] letters (start state 0);
+ *   delta    sum_i k[i] n[i] uint32 targets: DFA i's letter-major k[i] x n[i]
+ *            table starts at element sum_{j<i} k[j] n[j]; targets are local
+ *            to DFA i (< n[i]); NULL only if every k[i] = 0;
+ *   accept   sum_i n[i] bytes: DFA i's at offset sum_{j<i} n[j].
+ * delta and accept may each be host or device memory (checked once per buffer;
+ * host buffers are staged into the workspace with one copy each).  The caller
+ * keeps ownership of every buffer.  block_out, res, the workspace, the stream
+ * and every error (DFA_EINVAL for a bad size or target, DFA_EMAXROUNDS, ...)
+ * behave as in dfa_minimise_batch, whose results these calls reproduce DFA by
+ * DFA. */
+size_t dfa_batch_packed_workspace_size(uint32_t count, const uint32_t *n, const uint32_t *k, const uint32_t *delta,
+                                       const uint8_t *accept, const dfa_opts *opts);
+int dfa_minimise_batch_packed(uint32_t count, const uint32_t *n, const uint32_t *k, const uint32_t *delta,
+                              const uint8_t *accept, const dfa_opts *opts, uint32_t *block_out, dfa_result *res,
+                              void *workspace, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------- equivalence */
 

@@ -66,6 +66,10 @@ _SIGS = [
     ("dfa_batch_workspace_size", c_size_t, [POINTER(DfaT), c_uint32, POINTER(DfaOpts)]),
     ("dfa_minimise_batch", c_int, [POINTER(DfaT), c_uint32, POINTER(DfaOpts), c_void_p, POINTER(DfaResult), c_void_p,
                                    c_size_t, c_void_p]),
+    ("dfa_batch_packed_workspace_size", c_size_t, [c_uint32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                   POINTER(DfaOpts)]),
+    ("dfa_minimise_batch_packed", c_int, [c_uint32, c_void_p, c_void_p, c_void_p, c_void_p, POINTER(DfaOpts),
+                                          c_void_p, POINTER(DfaResult), c_void_p, c_size_t, c_void_p]),
     ("dfa_equivalent_workspace_size", c_size_t, [POINTER(DfaT), POINTER(DfaT), POINTER(DfaOpts)]),
     ("dfa_equivalent", c_int, [POINTER(DfaT), POINTER(DfaT), POINTER(DfaOpts), POINTER(c_int), POINTER(DfaResult),
                                c_void_p, c_size_t, c_void_p]),
@@ -212,17 +216,37 @@ def dfa_equivalent(a: DfaT, b: DfaT, opts: DfaOpts | None, workspace_ptr: int, w
     return st, bool(eq.value == 1), res
 
 
+def _dfa_array(dfas):
+    return dfas if isinstance(dfas, ctypes.Array) else (DfaT * len(dfas))(*dfas)
+
+
 def dfa_batch_workspace_size(dfas, opts: DfaOpts | None = None) -> int:
-    arr = (DfaT * len(dfas))(*dfas)
-    return int(lib().dfa_batch_workspace_size(arr, len(dfas), ctypes.byref(opts) if opts else None))
+    arr = _dfa_array(dfas)
+    return int(lib().dfa_batch_workspace_size(arr, len(arr), ctypes.byref(opts) if opts else None))
 
 
 def dfa_minimise_batch(dfas, opts: DfaOpts | None, block_out_ptr: int, workspace_ptr: int, ws_bytes: int,
                        stream: int | None):
-    arr = (DfaT * len(dfas))(*dfas)
-    res = (DfaResult * len(dfas))()
-    st = lib().dfa_minimise_batch(arr, len(dfas), ctypes.byref(opts) if opts else None, block_out_ptr, res,
+    arr = _dfa_array(dfas)
+    res = (DfaResult * len(arr))()
+    st = lib().dfa_minimise_batch(arr, len(arr), ctypes.byref(opts) if opts else None, block_out_ptr, res,
                                   workspace_ptr, ws_bytes, stream)
+    return st, list(res)
+
+
+def dfa_batch_packed_workspace_size(count: int, n_ptr: int, k_ptr: int, delta_ptr, accept_ptr: int,
+                                    opts: DfaOpts | None = None) -> int:
+    return int(lib().dfa_batch_packed_workspace_size(count, n_ptr, k_ptr, delta_ptr, accept_ptr,
+                                                     ctypes.byref(opts) if opts else None))
+
+
+def dfa_minimise_batch_packed(count: int, n_ptr: int, k_ptr: int, delta_ptr, accept_ptr: int,
+                              opts: DfaOpts | None, block_out_ptr: int, workspace_ptr: int, ws_bytes: int,
+                              stream: int | None):
+    res = (DfaResult * count)()
+    st = lib().dfa_minimise_batch_packed(count, n_ptr, k_ptr, delta_ptr, accept_ptr,
+                                         ctypes.byref(opts) if opts else None, block_out_ptr, res, workspace_ptr,
+                                         ws_bytes, stream)
     return st, list(res)
 
 
@@ -281,6 +305,7 @@ def minimise_batch(dfas, algo="moore", max_rounds=0, timeout_ns=0, schedule=-1, 
         d, kk = make_dfa(item[0], item[1])
         structs.append(d)
         keep.append(kk)
+    structs = _dfa_array(structs)
     o = make_opts(algo, max_rounds, timeout_ns, schedule, flags)
     total = sum(s.n for s in structs)
     if out is None:
@@ -292,6 +317,50 @@ def minimise_batch(dfas, algo="moore", max_rounds=0, timeout_ns=0, schedule=-1, 
     if workspace is None:
         workspace = _workspace(need)
     st, res = dfa_minimise_batch(structs, o, _ptr(out), _ptr(workspace), int(workspace.numel()), _stream(stream))
+    if check and st != DFA_OK:
+        raise DfaError(st, last_error())
+    return out, res
+
+
+def pack_batch(dfas, device="cuda"):
+    """The segment-offset form of a list of (delta (k, n), accept (n,)) pairs:
+    (n, k, delta, accept) with n, k numpy uint32 arrays and delta, accept the
+    concatenated arrays (each DFA's letter-major table in turn), as torch tensors
+    on `device` (numpy arrays if device is None)."""
+    ns = np.array([int(np.asarray(a).shape[0]) for _, a in dfas], dtype=np.uint32)
+    ks = np.array([int(np.asarray(d).shape[0]) for d, _ in dfas], dtype=np.uint32)
+    delta = np.concatenate([np.ascontiguousarray(d, dtype=np.uint32).reshape(-1) for d, _ in dfas])
+    accept = np.concatenate([np.ascontiguousarray(a, dtype=np.uint8).reshape(-1) for _, a in dfas])
+    if device is None:
+        return ns, ks, delta, accept
+    import torch
+    return ns, ks, torch.from_numpy(delta.view(np.int32)).to(device), torch.from_numpy(accept).to(device)
+
+
+def minimise_batch_packed(n, k, delta, accept, algo="moore", max_rounds=0, timeout_ns=0, schedule=-1, out=None,
+                          workspace=None, stream=None, check=True, flags=0):
+    """dfa_minimise_batch_packed over the segment-offset form (see pack_batch).
+    Returns (blocks, [DfaResult])."""
+    n = np.ascontiguousarray(n, dtype=np.uint32)
+    k = np.ascontiguousarray(k, dtype=np.uint32)
+    if n.shape != k.shape or n.ndim != 1:
+        raise ValueError("n and k must be 1-D arrays of the same length")
+    delta = _contig(delta, np.uint32)
+    accept = _contig(accept, np.uint8)
+    o = make_opts(algo, max_rounds, timeout_ns, schedule, flags)
+    count = int(n.shape[0])
+    dptr = _ptr(delta) if int(np.prod(delta.shape)) > 0 else None
+    args = (count, n.ctypes.data, k.ctypes.data, dptr, _ptr(accept))
+    if out is None:
+        import torch
+        out = torch.empty(int(n.sum(dtype=np.uint64)), dtype=torch.int32, device="cuda")
+    need = dfa_batch_packed_workspace_size(*args, o)
+    if need == 0:
+        raise DfaError(DFA_EINVAL, last_error() or "bad arguments")
+    if workspace is None:
+        workspace = _workspace(need)
+    st, res = dfa_minimise_batch_packed(*args, o, _ptr(out), _ptr(workspace), int(workspace.numel()),
+                                        _stream(stream))
     if check and st != DFA_OK:
         raise DfaError(st, last_error())
     return out, res

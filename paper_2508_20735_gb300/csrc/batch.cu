@@ -7,8 +7,9 @@
 // 2^ceil(log2(2 n_i)) slots of the renumbering table, so keys of different DFAs
 // never meet and labels stay narrow (a DFA with 65,536 states packs 17-bit
 // components).  Work is cut into tiles of at most kTile states that never
-// cross a DFA boundary; warps take tiles grid-stride and skip the tiles of
-// DFAs that have already converged.
+// cross a DFA boundary (listed on the device at the start of the launch from
+// each DFA's first tile number); warps take tiles grid-stride and skip the
+// tiles of DFAs that have already converged.
 //
 // Rounds.  Every pass packs each active state's signature into a key of its
 // own DFA's width and inserts it into its DFA's table region; a new slot counts
@@ -43,7 +44,6 @@ struct SegInfo {
   uint32_t state_off;      // first state in the batch's state space
   uint32_t log2S;          // table region of 2^log2S slots
   uint64_t table_off;      // first slot of the region
-  StagePlan plan1, planr;
 };
 
 struct Tile {
@@ -51,26 +51,27 @@ struct Tile {
 };
 
 // Per-DFA bookkeeping words.
-enum : uint32_t { SS_ACTIVE = 0, SS_PREV, SS_CHANGED, SS_EXECUTED, SS_FINAL, SS_B, SS_SEEN, SS_MAXED, SS_WORDS };
+enum : uint32_t { SS_ACTIVE = 0, SS_PREV, SS_CHANGED, SS_EXECUTED, SS_FINAL, SS_B, SS_SEEN, SS_MAXED, SS_W, SS_WORDS };
 
 struct BatchArgs {
   const SegInfo *segs;
   uint32_t nsegs;
-  const Tile *tiles;
+  const uint32_t *tile_off; // nsegs + 1: first tile of each DFA, then the tile count
+  Tile *tiles;             // ntiles, filled by the kernel
   uint32_t ntiles;
   uint32_t total_states;
   uint64_t total_slots;
-  uint32_t *lab[2];
-  uint32_t *fin;           // total_states: final labels gathered from either buffer
+  uint32_t *lab[2];        // labels, local to each DFA (< 2^log2S)
   uint32_t *tmp;           // total_states (multi-stage plans)
   u128 *table;
-  uint32_t *minrep;        // total_slots
-  uint8_t *flag;           // total_states
+  uint32_t *bm[2];         // direct rounds: one bit per table slot (ping-pong)
+  uint32_t *minrep;        // total_slots: smallest member per label (canonical numbering)
+  uint32_t *tile_cnt;      // ntiles: first members per tile (canonical numbering)
+  uint32_t *tile_pre;      // ntiles: their exclusive prefix sums
   uint32_t *partials;
   uint32_t *out;           // total_states
   uint32_t *cnt;           // nsegs x 3
   uint32_t *ss;            // nsegs x SS_WORDS
-  uint32_t *base;          // nsegs
   Ctrl *ctrl;
   uint32_t ebits, max_stages, max_rounds;
   uint32_t stop_discrete;  // 1: a DFA whose round leaves n blocks stops (no confirming round)
@@ -78,11 +79,89 @@ struct BatchArgs {
   unsigned long long timeout_ns, barrier_ns;
 };
 
+// A DFA's round is direct when its whole signature, (k+1) labels of w bits,
+// fits in log2S bits: the packed signature is then the new label itself.
+__device__ __forceinline__ bool batch_direct(const SegInfo &S, uint32_t w) {
+  return (uint64_t)(S.k + 1) * w <= S.log2S;
+}
+
+// Direct round over one tile: new label = packed signature; a bitmap over the
+// DFA's 2^log2S possible labels (bits [table_off, table_off + 2^log2S) of the
+// batch bitmap; table_off is a multiple of 64) counts the labels that appear,
+// one atomic per (warp, label).  Keys of at most kWarpBits bits are marked in
+// the warp's own 32-word shared bitmap first and merged once per tile, so that
+// the few words of such a DFA are not hit by every warp for every state.
+static constexpr uint32_t kWarpBits = 10;
+template <bool ROUND1>
+__device__ __forceinline__ void batch_direct_tile(const BatchArgs &A, const SegInfo &S, const Tile &T, uint32_t w,
+                                                 const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                                 uint32_t *bm, uint32_t *wbm, uint32_t r) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n = S.n, k = S.k;
+  const bool small = (k + 1) * w <= kWarpBits;
+  if (small) {
+    wbm[lane] = 0u;
+    __syncwarp();
+  }
+  const uint32_t *lsrc = src + S.state_off;
+  const unsigned long long keep = policy_evict_last();
+  uint32_t seen = 0, created = 0;
+  for (uint32_t base = 0; base < T.len; base += 32) {
+    const bool valid = base + lane < T.len;
+    const uint32_t q = T.start + (valid ? base + lane : 0u);
+    uint32_t key;
+    if (ROUND1) {
+      key = S.accept[q] != 0;
+      if (valid) seen |= key ? 1u : 2u;
+    } else {
+      key = lsrc[q];
+    }
+    uint32_t shift = w;
+    for (uint32_t a = 0; a < k; ++a) {
+      uint32_t d = S.delta[(size_t)a * n + q];
+      if (ROUND1 && d >= n) {
+        if (valid) atomicOr(&A.ctrl->err, ERR_BAD_DELTA);
+        d = 0;
+      }
+      const uint32_t c = ROUND1 ? (uint32_t)(S.accept[d] != 0) : ld_u32_hint(lsrc + d, keep);
+      key |= c << shift;
+      shift += w;
+    }
+    if (valid) dst[S.state_off + q] = key;
+    const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, valid ? key : 0xFFFFFFFFu) & vm;
+    if (valid && lane == (uint32_t)(__ffs(grp) - 1)) {
+      if (small) {
+        atomicOr(&wbm[key >> 5], 1u << (key & 31u));
+      } else {
+        const uint64_t pos = S.table_off + key;
+        const uint32_t bit = 1u << (pos & 31u);
+        if (!(atomicOr(&bm[pos >> 5], bit) & bit)) ++created;
+      }
+    }
+  }
+  if (small) {
+    __syncwarp();
+    const uint32_t v = wbm[lane];
+    if (v) created += __popc(v & ~atomicOr(&bm[(S.table_off >> 5) + lane], v));
+    __syncwarp();
+  }
+  const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, created);
+  if (lane == 0 && wsum) atomicAdd(&A.cnt[T.seg * 3 + r % 3], wsum);
+  if (ROUND1) {
+    const uint32_t wseen = __reduce_or_sync(0xFFFFFFFFu, seen);
+    if (lane == 0 && wseen) atomicOr(&A.ss[T.seg * SS_WORDS + SS_SEEN], wseen);
+  }
+}
+
+// Table round over one tile, stage `stage` of plan P: the signature's
+// components [cbeg, cend) (after the previous stage's slot) form a key of the
+// DFA's own table region; the slot is the new label.
 template <int VEC, bool ROUND1>
-__device__ __forceinline__ void batch_tile(const BatchArgs &A, const SegInfo &S, const Tile &T, uint32_t stage,
-                                          bool last, uint32_t epoch, const uint32_t *__restrict__ src,
-                                          uint32_t *__restrict__ dst, CtaCache *cache, uint32_t r) {
-  const StagePlan &P = ROUND1 ? S.plan1 : S.planr;
+__device__ __forceinline__ void batch_table_tile(const BatchArgs &A, const SegInfo &S, const Tile &T,
+                                                const StagePlan &P, uint32_t stage, bool last, uint32_t epoch,
+                                                const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                                CtaCache *cache, uint32_t r) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t n = S.n, total = S.k + 1, bits = P.bits;
   uint32_t cbeg, cend;
@@ -98,7 +177,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &A, const SegInfo &S,
   }
   const unsigned long long etag = (unsigned long long)epoch << (64 - A.ebits);
   const unsigned long long keep = policy_evict_last();
-  const uint32_t *lsrc = src + S.state_off;   // this DFA's labels (global slot numbers)
+  const uint32_t *lsrc = src + S.state_off;   // this DFA's labels (local numbers)
   u128 *table = A.table + S.table_off;
   uint32_t seen = 0, created_total = 0;
   for (uint32_t base = 0; base < T.len; base += 32u * VEC) {
@@ -130,7 +209,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &A, const SegInfo &S,
           c = S.accept[q] != 0;
           if (vv[v]) seen |= c ? 1u : 2u;
         } else {
-          c = lsrc[q] - (uint32_t)S.table_off;
+          c = lsrc[q];
         }
         put_bits(key[v], c, shift);
         shift += bits;
@@ -142,7 +221,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &A, const SegInfo &S,
           if (vv[v]) atomicOr(&A.ctrl->err, ERR_BAD_DELTA);
           d = 0;
         }
-        const uint32_t c = ROUND1 ? (uint32_t)(S.accept[d] != 0) : ld_u32_hint(lsrc + d, keep) - (uint32_t)S.table_off;
+        const uint32_t c = ROUND1 ? (uint32_t)(S.accept[d] != 0) : ld_u32_hint(lsrc + d, keep);
         put_bits(key[v], c, shift);
         shift += bits;
       }
@@ -164,7 +243,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &A, const SegInfo &S,
     for (int v = 0; v < VEC; ++v) {
       if (!vv[v]) continue;
       const uint32_t gq = S.state_off + qs[v];
-      if (last) dst[gq] = (uint32_t)S.table_off + lab[v];
+      if (last) dst[gq] = lab[v];
       else A.tmp[gq] = lab[v];
     }
   }
@@ -177,25 +256,68 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &A, const SegInfo &S,
   }
 }
 
+// Exclusive prefix sums of in[0, m) into out, by the whole grid: block b scans
+// a contiguous range, then adds the totals of the blocks before it.  `partials`
+// holds gridDim entries.  Returns false if a barrier failed.
+__device__ bool grid_excl_scan(const uint32_t *in, uint32_t *out, uint32_t m, uint32_t *partials, Ctrl *C,
+                               unsigned long long barrier_ns, uint32_t *s_red) {
+  uint32_t chunk = (m + gridDim.x - 1) / gridDim.x;
+  chunk = (chunk + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const uint64_t beg64 = (uint64_t)blockIdx.x * chunk;
+  const uint32_t beg = beg64 < m ? (uint32_t)beg64 : m;
+  const uint32_t end = (uint64_t)beg + chunk < m ? beg + chunk : m;
+  uint32_t running = 0;
+  for (uint32_t base = beg;; base += blockDim.x) {   // at least once: every thread takes part in the scan
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < end ? in[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_excl_scan(v, s_red, &total);
+    if (i < end) out[i] = running + ex;
+    running += total;
+    if (base + blockDim.x >= end) break;
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = running;
+  if (!grid_sync(C, barrier_ns)) return false;
+  uint32_t pre = 0;
+  for (uint32_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += partials[b];
+  pre = block_sum(pre, s_red);
+  for (uint32_t i = beg + threadIdx.x; i < end; i += blockDim.x) out[i] += pre;
+  return true;
+}
+
+// One state per lane: two blocks per SM (at most 64 registers); two states per
+// lane: one block per SM with room for the wider keys.
 template <int VEC>
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(BatchArgs A) {
   __shared__ uint32_t s_red[kBatchThreads / 32];
   __shared__ CtaCache cache;
+  __shared__ uint32_t s_wbm[kBatchThreads / 32][32];
   Ctrl *C = A.ctrl;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  const uint32_t gwarp = tid >> 5, nwarps = stride >> 5;
+  const uint32_t gwarp = tid >> 5, nwarps = stride >> 5, lane = threadIdx.x & 31u;
   if (leader) {
     const unsigned long long t = gtimer();
     C->t_start = t;
     C->deadline = t + A.timeout_ns;
   }
   const uint32_t emax = A.ebits >= 32 ? 0xFFFFFFFFu : ((1u << A.ebits) - 1u);
-  // clear tables; every DFA starts active
+  const uint64_t bm_words = (A.total_slots + 31) / 32;
+  // clear tables and round 1's bitmap; every DFA starts active with 1-bit labels
   for (uint64_t i = tid; i < A.total_slots; i += stride) reinterpret_cast<uint4 *>(A.table)[i] = make_uint4(0, 0, 0, 0);
+  for (uint64_t i = tid; i < bm_words; i += stride) A.bm[1][i] = 0u;
   for (uint32_t i = tid; i < A.nsegs; i += stride) {
     A.ss[i * SS_WORDS + SS_ACTIVE] = 1u;
     A.ss[i * SS_WORDS + SS_FINAL] = 1u;
+    A.ss[i * SS_WORDS + SS_W] = 1u;
+  }
+  // tile list: DFA i's tiles are tile_off[i] .. tile_off[i + 1) - 1, one warp per DFA
+  for (uint32_t i = gwarp; i < A.nsegs; i += nwarps) {
+    const uint32_t t0 = A.tile_off[i], nt = A.tile_off[i + 1] - t0, n = A.segs[i].n;
+    for (uint32_t j = lane; j < nt; j += 32) {
+      const uint32_t start = j * kTile;
+      A.tiles[t0 + j] = Tile{i, start, n - start < kTile ? n - start : kTile};
+    }
   }
   bool ok = grid_sync(C, A.barrier_ns);
   uint32_t epoch = 0, r;
@@ -203,6 +325,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs A) {
     const bool round1 = r == 1;
     const uint32_t *src = A.lab[(r - 1) & 1];
     uint32_t *dst = A.lab[r & 1];
+    // the bitmap of the next round starts clean (the one of the previous round is free now)
+    for (uint64_t i = tid; i < bm_words; i += stride) A.bm[(r + 1) & 1][i] = 0u;
     for (uint32_t s = 0; ok && s < A.max_stages; ++s) {
       if (epoch == emax) {
         for (uint64_t i = tid; i < A.total_slots; i += stride)
@@ -217,11 +341,19 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs A) {
         const Tile T = A.tiles[t];
         if (!ld_relaxed(&A.ss[T.seg * SS_WORDS + SS_ACTIVE])) continue;
         const SegInfo &S = A.segs[T.seg];
-        const StagePlan &P = round1 ? S.plan1 : S.planr;
+        const uint32_t w = A.ss[T.seg * SS_WORDS + SS_W];
+        if (batch_direct(S, w)) {
+          if (s != 0) continue;
+          uint32_t *wbm = s_wbm[threadIdx.x >> 5];
+          if (round1) batch_direct_tile<true>(A, S, T, w, src, dst, A.bm[r & 1], wbm, r);
+          else batch_direct_tile<false>(A, S, T, w, src, dst, A.bm[r & 1], wbm, r);
+          continue;
+        }
+        const StagePlan P = make_plan(S.k, w, S.log2S);
         if (s >= P.stages) continue;
         const bool last = s + 1 == P.stages;
-        if (round1) batch_tile<VEC, true>(A, S, T, s, last, epoch, src, dst, &cache, r);
-        else batch_tile<VEC, false>(A, S, T, s, last, epoch, src, dst, &cache, r);
+        if (round1) batch_table_tile<VEC, true>(A, S, T, P, s, last, epoch, src, dst, &cache, r);
+        else batch_table_tile<VEC, false>(A, S, T, P, s, last, epoch, src, dst, &cache, r);
       }
       ok = grid_sync(C, A.barrier_ns);
     }
@@ -232,17 +364,19 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs A) {
       uint32_t *w = A.ss + i * SS_WORDS;
       A.cnt[i * 3 + (r + 2) % 3] = 0u;
       if (!w[SS_ACTIVE]) continue;
+      const SegInfo &S = A.segs[i];
       const uint32_t B = A.cnt[i * 3 + r % 3];
       const uint32_t prev = round1 ? __popc(w[SS_SEEN]) : w[SS_PREV];
       w[SS_EXECUTED] = r;
       w[SS_FINAL] = r & 1;
       w[SS_B] = B;
+      w[SS_W] = batch_direct(S, w[SS_W]) ? (S.k + 1) * w[SS_W] : S.log2S;   // width of this round's labels
       if (B == prev) {
         w[SS_ACTIVE] = 0u;               // fixpoint (Algorithm 4's until-test)
       } else {
         w[SS_CHANGED] += 1;
         w[SS_PREV] = B;
-        if (A.stop_discrete && B == A.segs[i].n) {
+        if (A.stop_discrete && B == S.n) {
           w[SS_ACTIVE] = 0u;             // n singleton blocks cannot split any further
         } else if (A.max_rounds != 0u && r >= A.max_rounds) {
           w[SS_ACTIVE] = 0u;
@@ -260,35 +394,97 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs A) {
     if (leader) C->cnt[(r + 2) % 3] = 0u;
     if (active == 0u) break;
   }
+
+  // Canonical numbering per DFA: block id = rank of its smallest state within
+  // the DFA.  A DFA with n blocks is numbered by its states; the others find
+  // each label's smallest state in their own slice of minrep (2^log2S entries
+  // at table_off), count first members per tile, and rank them by a scan over
+  // the tiles.
   if (ok) {
-    // final labels of every DFA into one buffer
     for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
-      const uint32_t *srcf = A.lab[A.ss[T.seg * SS_WORDS + SS_FINAL]];
-      for (uint32_t i = threadIdx.x & 31u; i < T.len; i += 32) {
-        const uint32_t gq = S.state_off + T.start + i;
-        A.fin[gq] = srcf[gq];
+      if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
+      const uint64_t region = 1ull << S.log2S;
+      const uint32_t nt = A.tile_off[T.seg + 1] - A.tile_off[T.seg], j = t - A.tile_off[T.seg];
+      const uint64_t per = (region + nt - 1) / nt, lo = (uint64_t)j * per;
+      const uint64_t hi = lo + per < region ? lo + per : region;
+      for (uint64_t i = lo + lane; i < hi; i += 32) A.minrep[S.table_off + i] = 0xFFFFFFFFu;
+    }
+    ok = grid_sync(C, A.barrier_ns);
+  }
+  if (ok) {
+    for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+      const Tile T = A.tiles[t];
+      const SegInfo &S = A.segs[T.seg];
+      if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
+      const uint32_t *fl = A.lab[A.ss[T.seg * SS_WORDS + SS_FINAL]] + S.state_off;
+      for (uint32_t base = 0; base < T.len; base += 32) {
+        const bool valid = base + lane < T.len;
+        const uint32_t q = T.start + base + lane;
+        const uint32_t l = valid ? fl[q] : 0u;
+        // lanes hold consecutive states: the lowest lane of a label group is its smallest state
+        const unsigned grp = __match_any_sync(0xFFFFFFFFu, l) & __ballot_sync(0xFFFFFFFFu, valid);
+        if (valid && lane == (uint32_t)(__ffs(grp) - 1)) atomicMin(&A.minrep[S.table_off + l], q);
       }
     }
     ok = grid_sync(C, A.barrier_ns);
   }
   if (ok) {
-    ok = canonicalise(CanonArgs{A.total_states, A.fin, (size_t)A.total_slots, A.minrep, A.flag, A.partials, A.out,
-                                C, A.barrier_ns, 0u},
-                      0xFFFFFFFFu, s_red);
+    for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+      const Tile T = A.tiles[t];
+      const SegInfo &S = A.segs[T.seg];
+      uint32_t c = T.len;
+      if (A.ss[T.seg * SS_WORDS + SS_B] != S.n) {
+        const uint32_t *fl = A.lab[A.ss[T.seg * SS_WORDS + SS_FINAL]] + S.state_off;
+        c = 0;
+        for (uint32_t base = 0; base < T.len; base += 32) {
+          const uint32_t q = T.start + base + lane;
+          const bool first = base + lane < T.len && A.minrep[S.table_off + fl[q]] == q;
+          c += __popc(__ballot_sync(0xFFFFFFFFu, first));
+        }
+      }
+      if (lane == 0) A.tile_cnt[t] = c;
+    }
+    ok = grid_sync(C, A.barrier_ns);
   }
+  if (ok) ok = grid_excl_scan(A.tile_cnt, A.tile_pre, A.ntiles, A.partials, C, A.barrier_ns, s_red);
   if (ok) ok = grid_sync(C, A.barrier_ns);
   if (ok) {
-    // blocks of earlier DFAs precede DFA i's: its first state's number is its offset
-    for (uint32_t i = tid; i < A.nsegs; i += stride) A.base[i] = A.out[A.segs[i].state_off];
+    for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+      const Tile T = A.tiles[t];
+      const SegInfo &S = A.segs[T.seg];
+      uint32_t *o = A.out + S.state_off;
+      if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) {
+        for (uint32_t i = lane; i < T.len; i += 32) o[T.start + i] = T.start + i;
+        continue;
+      }
+      const uint32_t *fl = A.lab[A.ss[T.seg * SS_WORDS + SS_FINAL]] + S.state_off;
+      uint32_t rank = A.tile_pre[t] - A.tile_pre[A.tile_off[T.seg]];
+      for (uint32_t base = 0; base < T.len; base += 32) {
+        const uint32_t q = T.start + base + lane;
+        const bool valid = base + lane < T.len;
+        const uint32_t l = valid ? fl[q] : 0u;
+        const bool first = valid && A.minrep[S.table_off + l] == q;
+        const unsigned fm = __ballot_sync(0xFFFFFFFFu, first);
+        // every lane has read minrep[l] above before any lane overwrites it
+        __syncwarp();
+        if (first) A.minrep[S.table_off + l] = 0x80000000u | (rank + __popc(fm & ((1u << lane) - 1u)));
+        rank += __popc(fm);
+      }
+    }
     ok = grid_sync(C, A.barrier_ns);
   }
   if (ok) {
     for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
       const Tile T = A.tiles[t];
-      const uint32_t off = A.segs[T.seg].state_off + T.start, b = A.base[T.seg];
-      for (uint32_t i = threadIdx.x & 31u; i < T.len; i += 32) A.out[off + i] -= b;
+      const SegInfo &S = A.segs[T.seg];
+      if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
+      const uint32_t *fl = A.lab[A.ss[T.seg * SS_WORDS + SS_FINAL]] + S.state_off;
+      for (uint32_t i = lane; i < T.len; i += 32) {
+        const uint32_t q = T.start + i;
+        A.out[S.state_off + q] = A.minrep[S.table_off + fl[q]] & 0x7FFFFFFFu;
+      }
     }
   }
   if (leader) {
@@ -300,19 +496,46 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs A) {
 // ------------------------------------------------------------------ host side
 
 struct BatchLayout {
-  size_t ctrl, segs, tiles, lab0, lab1, fin, tmp, table, minrep, flag, partials, out, cnt, ss, base, stage, total;
+  size_t ctrl, segs, tile_off, tiles, lab0, lab1, tmp, table, bm0, bm1, minrep, tile_cnt, tile_pre, partials, out, cnt, ss, stage,
+      total;
   uint64_t total_states, total_slots;
   uint32_t ntiles, max_stages, ebits;
   size_t stage_bytes;
 };
 
-static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, std::vector<SegInfo> *segs_out,
-                                std::vector<Tile> *tiles_out, std::vector<size_t> *stage_off) {
+// Where the inputs of a batch live: host[2i] / host[2i + 1] tell whether DFA
+// i's delta / accept are host memory, to be staged into the workspace.  With
+// `packed`, the DFAs' arrays are consecutive pieces of one delta buffer and one
+// accept buffer (in DFA order); host ones are staged as two copies, keeping
+// that order.
+struct BatchInputs {
+  std::vector<uint8_t> host;
+  bool packed = false;
+};
+
+static BatchInputs classify_inputs(const dfa_t *dfas, uint32_t count) {
+  BatchInputs in;
+  in.host.resize((size_t)count * 2);
+  for (uint32_t i = 0; i < count; ++i) {
+    in.host[2 * i] = dfas[i].k > 0 && !is_device_ptr(dfas[i].delta);
+    in.host[2 * i + 1] = !is_device_ptr(dfas[i].accept);
+  }
+  return in;
+}
+
+static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchInputs &in,
+                                std::vector<SegInfo> *segs_out, std::vector<uint32_t> *tile_off_out,
+                                std::vector<size_t> *stage_off) {
   BatchLayout L{};
   uint64_t st = 0, sl = 0;
   uint32_t ntiles = 0, max_stages = 1, ebits = 32;
   size_t stage_bytes = 0;
   bool multi = false;
+  size_t packed_delta_bytes = 0;
+  if (in.packed)
+    for (uint32_t i = 0; i < count; ++i)
+      if (in.host[2 * i]) packed_delta_bytes += (size_t)dfas[i].k * dfas[i].n * 4;
+  size_t pd = 0, pa = (packed_delta_bytes + 255) / 256 * 256;
   for (uint32_t i = 0; i < count; ++i) {
     const dfa_t &d = dfas[i];
     SegInfo s{};
@@ -321,28 +544,45 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, std::vector<S
     s.state_off = (uint32_t)st;
     s.log2S = ceil_log2((uint64_t)d.n * 2 < 64 ? 64 : (uint64_t)d.n * 2);
     s.table_off = sl;
-    s.plan1 = make_plan(d.k, 1, s.log2S);
-    s.planr = make_plan(d.k, s.log2S, s.log2S);
-    max_stages = std::max({max_stages, s.plan1.stages, s.planr.stages});
-    ebits = std::min({ebits, s.plan1.ebits, s.planr.ebits});
-    multi |= s.plan1.stages > 1 || s.planr.stages > 1;
-    const uint32_t tiles_i = (d.n + kTile - 1) / kTile;
-    if (tiles_out)
-      for (uint32_t t = 0; t < tiles_i; ++t)
-        tiles_out->push_back(Tile{i, t * kTile, std::min(kTile, d.n - t * kTile)});
-    ntiles += tiles_i;
-    // host-resident arrays are staged into the workspace
-    const bool hd = d.k > 0 && !is_device_ptr(d.delta), ha = !is_device_ptr(d.accept);
-    if (stage_off) {
-      stage_off->push_back(hd ? stage_bytes : SIZE_MAX);
+    // label widths a DFA goes through: 1 bit, then (k+1) times wider while the
+    // rounds are direct, then log2S bits (table rounds) for good; the table
+    // rounds' plans decide the stage count and the epoch bits left free
+    if (d.k > 0) {
+      uint64_t w = 1;
+      while ((uint64_t)(d.k + 1) * w <= s.log2S) w *= d.k + 1;   // direct rounds
+      for (;;) {
+        const StagePlan p = make_plan(d.k, (uint32_t)w, s.log2S);
+        max_stages = std::max(max_stages, p.stages);
+        ebits = std::min(ebits, p.ebits);
+        multi |= p.stages > 1;
+        if (w == s.log2S) break;
+        w = s.log2S;
+      }
     }
-    if (hd) stage_bytes += ((size_t)d.k * d.n * 4 + 255) / 256 * 256;
-    if (stage_off) stage_off->push_back(ha ? stage_bytes : SIZE_MAX);
-    if (ha) stage_bytes += ((size_t)d.n + 255) / 256 * 256;
+    if (tile_off_out) tile_off_out->push_back(ntiles);
+    ntiles += (d.n + kTile - 1) / kTile;
+    // host-resident arrays are staged into the workspace
+    const bool hd = in.host[2 * i], ha = in.host[2 * i + 1];
+    const size_t db = (size_t)d.k * d.n * 4, ab = d.n;
+    if (in.packed) {
+      if (stage_off) {
+        stage_off->push_back(hd ? pd : SIZE_MAX);
+        stage_off->push_back(ha ? pa : SIZE_MAX);
+      }
+      if (hd) pd += db;
+      if (ha) pa += ab;
+      stage_bytes = pa;
+    } else {
+      if (stage_off) stage_off->push_back(hd ? stage_bytes : SIZE_MAX);
+      if (hd) stage_bytes += (db + 255) / 256 * 256;
+      if (stage_off) stage_off->push_back(ha ? stage_bytes : SIZE_MAX);
+      if (ha) stage_bytes += (ab + 255) / 256 * 256;
+    }
     st += d.n;
     sl += (uint64_t)1 << s.log2S;
     if (segs_out) segs_out->push_back(s);
   }
+  if (tile_off_out) tile_off_out->push_back(ntiles);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t at = off;
@@ -356,19 +596,21 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, std::vector<S
   L.ebits = ebits;
   L.ctrl = take(sizeof(Ctrl));
   L.segs = take(sizeof(SegInfo) * count);
-  L.tiles = take(sizeof(Tile) * ntiles);
+  L.tile_off = take(((size_t)count + 1) * 4);
+  L.tiles = take((size_t)ntiles * sizeof(Tile));
   L.lab0 = take(st * 4);
   L.lab1 = take(st * 4);
-  L.fin = take(st * 4);
   L.tmp = multi ? take(st * 4) : SIZE_MAX;
   L.table = take(sl * 16);
+  L.bm0 = take((sl + 31) / 32 * 4);
+  L.bm1 = take((sl + 31) / 32 * 4);
   L.minrep = take(sl * 4);
-  L.flag = take(st);
+  L.tile_cnt = take((size_t)ntiles * 4);
+  L.tile_pre = take((size_t)ntiles * 4);
   L.partials = take(kMaxGridB * 4);
   L.out = take(st * 4);
   L.cnt = take((size_t)count * 3 * 4);
   L.ss = take((size_t)count * SS_WORDS * 4);
-  L.base = take((size_t)count * 4);
   L.stage_bytes = stage_bytes;
   L.stage = take(stage_bytes);
   L.total = off;
@@ -467,52 +709,87 @@ static std::string tune_key(uint64_t states, uint32_t count, uint32_t kmax) {
 
 using namespace dfa;
 
-extern "C" {
-
-size_t dfa_batch_workspace_size(const dfa_t *dfas, uint32_t count, const dfa_opts *opts) {
-  (void)opts;
-  if (!dfas || count == 0) return 0;
-  uint64_t total = 0;
+// Checks a batch and its sizes; fills total states and the largest k.
+static int check_batch(const dfa_t *dfas, uint32_t count, uint64_t *total, uint32_t *kmax) {
+  if (!dfas || count == 0) return fail(DFA_EINVAL, "empty batch");
+  *total = 0;
+  *kmax = 0;
   for (uint32_t i = 0; i < count; ++i) {
-    if (check_dfa(&dfas[i], "dfas[i]") != DFA_OK) return 0;
-    total += dfas[i].n;
+    const int rc = check_dfa(&dfas[i], "dfas[i]");
+    if (rc != DFA_OK) return fail(rc, "dfa %u: %s", i, dfa_last_error());
+    *total += dfas[i].n;
+    *kmax = std::max(*kmax, dfas[i].k);
   }
-  if (total > DFA_MAX_STATES) return 0;
-  const BatchLayout L = batch_layout(dfas, count, nullptr, nullptr, nullptr);
+  if (*total > DFA_MAX_STATES)
+    return fail(DFA_EINVAL, "batch of %llu states exceeds %u", (unsigned long long)*total, DFA_MAX_STATES);
+  return DFA_OK;
+}
+
+static size_t batch_workspace_impl(const dfa_t *dfas, uint32_t count, const BatchInputs &in) {
+  uint64_t total;
+  uint32_t kmax;
+  if (check_batch(dfas, count, &total, &kmax) != DFA_OK) return 0;
+  const BatchLayout L = batch_layout(dfas, count, in, nullptr, nullptr, nullptr);
   if (L.total_slots > 0xFFFFFFFFull) return 0;
   return L.total;
 }
 
-static int run_batch(const dfa_t *dfas, uint32_t count, const dfa_opts &o, uint32_t *block_out, dfa_result *res,
-                     char *ws, size_t ws_bytes, cudaStream_t st, uint32_t vec, uint64_t *device_ns) {
+static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, const dfa_opts &o,
+                     uint32_t *block_out, dfa_result *res, char *ws, size_t ws_bytes, cudaStream_t st, uint32_t vec,
+                     uint64_t *device_ns) {
   std::vector<SegInfo> segs;
-  std::vector<Tile> tiles;
+  std::vector<uint32_t> tile_off;
   std::vector<size_t> stage_off;
-  const BatchLayout L = batch_layout(dfas, count, &segs, &tiles, &stage_off);
+  const BatchLayout L = batch_layout(dfas, count, in, &segs, &tile_off, &stage_off);
   if (L.total_slots > 0xFFFFFFFFull) return fail(DFA_EINVAL, "batch too large for 32-bit labels");
   if (ws_bytes < L.total) return fail(DFA_EINVAL, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
   cudaError_t e;
+  if (in.packed) {
+    // one copy per host buffer: the pieces are consecutive in both places
+    size_t db = 0, ab = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+      if (in.host[2 * i]) db += (size_t)dfas[i].k * dfas[i].n * 4;
+      if (in.host[2 * i + 1]) ab += dfas[i].n;
+    }
+    const uint32_t first_d = [&] {
+      for (uint32_t i = 0; i < count; ++i)
+        if (dfas[i].k > 0) return i;
+      return count;
+    }();
+    if (db > 0) {
+      e = cudaMemcpyAsync(ws + L.stage + stage_off[2 * first_d], dfas[first_d].delta, db, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "copy packed delta to device");
+    }
+    if (ab > 0) {
+      e = cudaMemcpyAsync(ws + L.stage + stage_off[1], dfas[0].accept, ab, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "copy packed accept to device");
+    }
+  }
   for (uint32_t i = 0; i < count; ++i) {
     const dfa_t &d = dfas[i];
     segs[i].delta = d.delta;
     segs[i].accept = d.accept;
     if (stage_off[2 * i] != SIZE_MAX) {
       char *p = ws + L.stage + stage_off[2 * i];
-      e = cudaMemcpyAsync(p, d.delta, (size_t)d.k * d.n * 4, cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) return cuda_fail(e, "copy delta to device");
+      if (!in.packed) {
+        e = cudaMemcpyAsync(p, d.delta, (size_t)d.k * d.n * 4, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy delta to device");
+      }
       segs[i].delta = reinterpret_cast<const uint32_t *>(p);
     }
     if (stage_off[2 * i + 1] != SIZE_MAX) {
       char *p = ws + L.stage + stage_off[2 * i + 1];
-      e = cudaMemcpyAsync(p, d.accept, d.n, cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) return cuda_fail(e, "copy accept to device");
+      if (!in.packed) {
+        e = cudaMemcpyAsync(p, d.accept, d.n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy accept to device");
+      }
       segs[i].accept = reinterpret_cast<const uint8_t *>(p);
     }
   }
   e = cudaMemcpyAsync(ws + L.segs, segs.data(), sizeof(SegInfo) * count, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "copy segment table");
-  e = cudaMemcpyAsync(ws + L.tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "copy tile table");
+  e = cudaMemcpyAsync(ws + L.tile_off, tile_off.data(), tile_off.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy tile offsets");
   e = cudaMemsetAsync(ws + L.cnt, 0, (size_t)count * 3 * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.ss, 0, (size_t)count * SS_WORDS * 4, st);
   if (e != cudaSuccess) return cuda_fail(e, "clear batch bookkeeping");
@@ -520,22 +797,24 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const dfa_opts &o, uint3
   BatchArgs a{};
   a.segs = reinterpret_cast<const SegInfo *>(ws + L.segs);
   a.nsegs = count;
-  a.tiles = reinterpret_cast<const Tile *>(ws + L.tiles);
+  a.tile_off = reinterpret_cast<const uint32_t *>(ws + L.tile_off);
+  a.tiles = reinterpret_cast<Tile *>(ws + L.tiles);
   a.ntiles = L.ntiles;
   a.total_states = (uint32_t)L.total_states;
   a.total_slots = L.total_slots;
   a.lab[0] = reinterpret_cast<uint32_t *>(ws + L.lab0);
   a.lab[1] = reinterpret_cast<uint32_t *>(ws + L.lab1);
-  a.fin = reinterpret_cast<uint32_t *>(ws + L.fin);
   a.tmp = L.tmp == SIZE_MAX ? nullptr : reinterpret_cast<uint32_t *>(ws + L.tmp);
   a.table = reinterpret_cast<u128 *>(ws + L.table);
+  a.bm[0] = reinterpret_cast<uint32_t *>(ws + L.bm0);
+  a.bm[1] = reinterpret_cast<uint32_t *>(ws + L.bm1);
   a.minrep = reinterpret_cast<uint32_t *>(ws + L.minrep);
-  a.flag = reinterpret_cast<uint8_t *>(ws + L.flag);
+  a.tile_cnt = reinterpret_cast<uint32_t *>(ws + L.tile_cnt);
+  a.tile_pre = reinterpret_cast<uint32_t *>(ws + L.tile_pre);
   a.partials = reinterpret_cast<uint32_t *>(ws + L.partials);
   a.out = ho ? reinterpret_cast<uint32_t *>(ws + L.out) : block_out;
   a.cnt = reinterpret_cast<uint32_t *>(ws + L.cnt);
   a.ss = reinterpret_cast<uint32_t *>(ws + L.ss);
-  a.base = reinterpret_cast<uint32_t *>(ws + L.base);
   a.ctrl = reinterpret_cast<Ctrl *>(ws + L.ctrl);
   a.ebits = L.ebits;
   a.max_stages = L.max_stages;
@@ -585,27 +864,20 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const dfa_opts &o, uint3
   return overall;
 }
 
-int dfa_minimise_batch(const dfa_t *dfas, uint32_t count, const dfa_opts *opts, uint32_t *block_out,
-                       dfa_result *res, void *workspace, size_t ws_bytes, void *stream) {
-  if (!dfas || count == 0) return fail(DFA_EINVAL, "empty batch");
-  uint64_t total = 0;
-  uint32_t kmax = 0;
-  for (uint32_t i = 0; i < count; ++i) {
-    const int rc = check_dfa(&dfas[i], "dfas[i]");
-    if (rc != DFA_OK) return fail(rc, "dfa %u: %s", i, dfa_last_error());
-    total += dfas[i].n;
-    kmax = std::max(kmax, dfas[i].k);
-  }
-  if (total > DFA_MAX_STATES) return fail(DFA_EINVAL, "batch of %llu states exceeds %u", (unsigned long long)total,
-                                          DFA_MAX_STATES);
+static int minimise_batch_impl(const dfa_t *dfas, uint32_t count, const BatchInputs &in, const dfa_opts *opts,
+                               uint32_t *block_out, dfa_result *res, void *workspace, size_t ws_bytes, void *stream) {
+  uint64_t total;
+  uint32_t kmax;
+  const int rc0 = check_batch(dfas, count, &total, &kmax);
+  if (rc0 != DFA_OK) return rc0;
   if (!block_out) return fail(DFA_EINVAL, "block_out is NULL");
   if (!workspace || !aligned(workspace, 256)) return fail(DFA_EINVAL, "workspace NULL or not 256-byte aligned");
   const dfa_opts o = default_opts(opts);
   if (o.algo != DFA_ALGO_MOORE) return fail(DFA_EINVAL, "batches use signature refinement (algo 0)");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char *ws = static_cast<char *>(workspace);
   if (o.schedule == 0 || o.schedule == 1)
-    return run_batch(dfas, count, o, block_out, res, static_cast<char *>(workspace), ws_bytes, st,
-                     o.schedule == 1 ? 2u : 1u, nullptr);
+    return run_batch(dfas, count, in, o, block_out, res, ws, ws_bytes, st, o.schedule == 1 ? 2u : 1u, nullptr);
   // autotune
   const std::string key = tune_key(total, count, kmax);
   int choice = -1;
@@ -619,8 +891,7 @@ int dfa_minimise_batch(const dfa_t *dfas, uint32_t count, const dfa_opts *opts, 
     uint64_t best = ~0ull;
     for (int s = 0; s < 2; ++s) {
       uint64_t ns = 0;
-      const int rc = run_batch(dfas, count, o, block_out, res, static_cast<char *>(workspace), ws_bytes, st,
-                               s == 1 ? 2u : 1u, &ns);
+      const int rc = run_batch(dfas, count, in, o, block_out, res, ws, ws_bytes, st, s == 1 ? 2u : 1u, &ns);
       if (rc != DFA_OK && rc != DFA_EMAXROUNDS) return rc;
       if (ns < best) {
         best = ns;
@@ -631,8 +902,76 @@ int dfa_minimise_batch(const dfa_t *dfas, uint32_t count, const dfa_opts *opts, 
     g_tune[key] = choice;
     tune_save();
   }
-  return run_batch(dfas, count, o, block_out, res, static_cast<char *>(workspace), ws_bytes, st,
-                   choice == 1 ? 2u : 1u, nullptr);
+  return run_batch(dfas, count, in, o, block_out, res, ws, ws_bytes, st, choice == 1 ? 2u : 1u, nullptr);
+}
+
+// dfa_t entries of a packed batch (pieces of the two buffers, in DFA order).
+static int packed_dfas(uint32_t count, const uint32_t *n, const uint32_t *k, const uint32_t *delta,
+                       const uint8_t *accept, std::vector<dfa_t> *dfas, BatchInputs *in) {
+  if (count == 0) return fail(DFA_EINVAL, "empty batch");
+  if (!n || !k) return fail(DFA_EINVAL, "n or k is NULL");
+  if (!accept) return fail(DFA_EINVAL, "accept is NULL");
+  dfas->resize(count);
+  size_t od = 0, oa = 0;
+  bool any_letters = false;
+  for (uint32_t i = 0; i < count; ++i) {
+    dfa_t &d = (*dfas)[i];
+    d.n = n[i];
+    d.k = k[i];
+    d.start = 0;
+    any_letters |= k[i] > 0;
+    d.delta = k[i] > 0 && delta ? delta + od : nullptr;
+    d.accept = accept + oa;
+    od += (size_t)k[i] * n[i];
+    oa += n[i];
+  }
+  if (any_letters && !delta) return fail(DFA_EINVAL, "delta is NULL");
+  in->packed = true;
+  const bool hd = any_letters && !is_device_ptr(delta), ha = !is_device_ptr(accept);
+  in->host.resize((size_t)count * 2);
+  for (uint32_t i = 0; i < count; ++i) {
+    in->host[2 * i] = hd && k[i] > 0;
+    in->host[2 * i + 1] = ha;
+  }
+  return DFA_OK;
+}
+
+extern "C" {
+
+size_t dfa_batch_workspace_size(const dfa_t *dfas, uint32_t count, const dfa_opts *opts) {
+  (void)opts;
+  if (!dfas || count == 0) return 0;
+  return batch_workspace_impl(dfas, count, classify_inputs(dfas, count));
+}
+
+int dfa_minimise_batch(const dfa_t *dfas, uint32_t count, const dfa_opts *opts, uint32_t *block_out,
+                       dfa_result *res, void *workspace, size_t ws_bytes, void *stream) {
+  if (!dfas || count == 0) return fail(DFA_EINVAL, "empty batch");
+  uint64_t total;
+  uint32_t kmax;
+  const int rc = check_batch(dfas, count, &total, &kmax);
+  if (rc != DFA_OK) return rc;
+  return minimise_batch_impl(dfas, count, classify_inputs(dfas, count), opts, block_out, res, workspace, ws_bytes,
+                             stream);
+}
+
+size_t dfa_batch_packed_workspace_size(uint32_t count, const uint32_t *n, const uint32_t *k, const uint32_t *delta,
+                                       const uint8_t *accept, const dfa_opts *opts) {
+  (void)opts;
+  std::vector<dfa_t> dfas;
+  BatchInputs in;
+  if (packed_dfas(count, n, k, delta, accept, &dfas, &in) != DFA_OK) return 0;
+  return batch_workspace_impl(dfas.data(), count, in);
+}
+
+int dfa_minimise_batch_packed(uint32_t count, const uint32_t *n, const uint32_t *k, const uint32_t *delta,
+                              const uint8_t *accept, const dfa_opts *opts, uint32_t *block_out, dfa_result *res,
+                              void *workspace, size_t ws_bytes, void *stream) {
+  std::vector<dfa_t> dfas;
+  BatchInputs in;
+  const int rc = packed_dfas(count, n, k, delta, accept, &dfas, &in);
+  if (rc != DFA_OK) return rc;
+  return minimise_batch_impl(dfas.data(), count, in, opts, block_out, res, workspace, ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -21,28 +21,6 @@ namespace dfa {
 
 static constexpr int kThreads = 512;
 
-__host__ __device__ StagePlan make_plan(uint32_t k, uint32_t bits, uint32_t carry) {
-  StagePlan p{};
-  const uint32_t total = k + 1;     // own block + one per letter
-  const uint32_t cap = 125;         // key bits; at least 3 bits remain for the epoch
-  p.bits = bits;
-  p.carry = carry;
-  if ((uint64_t)total * bits <= cap) {
-    p.first = total;
-    p.per = 1;
-    p.stages = 1;
-    const uint32_t used = total * bits;
-    p.ebits = (128 - used) > 32 ? 32 : (128 - used);
-  } else {
-    p.first = cap / bits;
-    p.per = (cap - carry) / bits;
-    p.stages = 1 + (total - p.first + p.per - 1) / p.per;
-    const uint32_t used = p.first * bits > carry + p.per * bits ? p.first * bits : carry + p.per * bits;
-    p.ebits = (128 - used) > 32 ? 32 : (128 - used);
-  }
-  return p;
-}
-
 // Vector loads/stores of VEC consecutive 32-bit values (VEC*4-byte aligned).
 template <int VEC>
 __device__ __forceinline__ void load_vec(const uint32_t *p, uint32_t (&x)[VEC]) {

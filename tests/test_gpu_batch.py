@@ -123,3 +123,67 @@ def test_batch_bad_delta(g):
     B.delta[1][7] = 50
     with pytest.raises(g.DfaError):
         _batch(g, [A, B])
+
+
+# ---------------------------------------------------------------- packed (segment-offset) form
+
+def _packed(g, dfas, device="cuda", **kw):
+    n, k, d, a = g.pack_batch([(A.delta, A.accept) for A in dfas], device=device)
+    out, res = g.minimise_batch_packed(n, k, d, a, **kw)
+    blocks = out.cpu().numpy().view(np.uint32)
+    offs = np.concatenate([[0], np.cumsum([A.n for A in dfas])])
+    return [blocks[offs[i]:offs[i + 1]] for i in range(len(dfas))], res
+
+
+@pytest.mark.parametrize("device", ["cuda", None])
+def test_packed_equals_list_form(g, device):
+    dfas = _mixed()
+    pb, pr = _packed(g, dfas, device=device)
+    lb, lr = _batch(g, dfas)
+    for A, x, y, rx, ry in zip(dfas, pb, lb, pr, lr):
+        assert np.array_equal(x, y)
+        assert (rx.num_blocks, rx.rounds_changed, rx.rounds_executed) == \
+            (ry.num_blocks, ry.rounds_changed, ry.rounds_executed)
+        ref = oracle.moore(A.delta, A.accept)
+        assert np.array_equal(x, ref.block)
+
+
+@pytest.mark.parametrize("device", ["cuda", None])
+def test_packed_letterless_dfas(g, device):
+    """DFAs with no letters anywhere in the batch, first included (the packed
+    delta then starts at the first DFA that has letters)."""
+    dfas = [dfagen.random_dfa(5, 0, 0.5, 1), dfagen.random_dfa(300, 3, 0.5, 2), dfagen.random_dfa(7, 0, 0.5, 3),
+            dfagen.random_dfa(1000, 2, 0.3, 4)]
+    pb, pr = _packed(g, dfas, device=device)
+    for A, b, r in zip(dfas, pb, pr):
+        ref = oracle.moore(A.delta, A.accept)
+        assert np.array_equal(b, ref.block)
+        assert (r.rounds_changed, r.rounds_executed) == (ref.rounds_changed, ref.rounds_executed)
+    only = [dfagen.random_dfa(9, 0, 0.5, 5), dfagen.random_dfa(4, 0, 0.5, 6)]
+    ob, _ = _packed(g, only, device=device)
+    for A, b in zip(only, ob):
+        assert np.array_equal(b, oracle.moore(A.delta, A.accept).block)
+
+
+def test_packed_bad_target_and_sizes(g):
+    A = dfagen.random_dfa(100, 2, 0.5, 3)
+    B = dfagen.random_dfa(50, 2, 0.5, 4)
+    n, k, d, a = g.pack_batch([(A.delta, A.accept), (B.delta, B.accept)])
+    d[2 * 100 + 7] = 50                      # DFA 1's targets are local: 50 is out of range
+    with pytest.raises(g.DfaError) as e:
+        g.minimise_batch_packed(n, k, d, a)
+    assert e.value.status == g.DFA_EINVAL
+    n2 = n.copy()
+    n2[1] = 0
+    with pytest.raises(g.DfaError):
+        g.minimise_batch_packed(n2, k, d, a)
+
+
+def test_packed_4096_full_size(g):
+    """The 4,096-DFA workload in packed form equals the list form, DFA by DFA."""
+    dfas = dfagen.batch_dfas(4096, 64, 65_536, 2, 8, 0.3, 4)
+    pb, pr = _packed(g, dfas)
+    lb, lr = _batch(g, dfas)
+    for i in range(len(dfas)):
+        assert np.array_equal(pb[i], lb[i]), i
+        assert (pr[i].num_blocks, pr[i].rounds_executed) == (lr[i].num_blocks, lr[i].rounds_executed), i
