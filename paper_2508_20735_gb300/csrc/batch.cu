@@ -43,6 +43,7 @@ struct SegInfo {
   uint32_t n, k;
   uint32_t state_off;      // first state in the batch's state space
   uint32_t log2S;          // table region of 2^log2S slots
+  uint32_t wid;            // bits of a local state number (labels of filter rounds)
   uint64_t table_off;      // first slot of the region
 };
 
@@ -51,7 +52,13 @@ struct Tile {
 };
 
 // Per-DFA bookkeeping words.
-enum : uint32_t { SS_ACTIVE = 0, SS_PREV, SS_CHANGED, SS_EXECUTED, SS_FINAL, SS_B, SS_SEEN, SS_MAXED, SS_W, SS_WORDS };
+enum : uint32_t {
+  SS_ACTIVE = 0, SS_PREV, SS_CHANGED, SS_EXECUTED, SS_FINAL, SS_B, SS_SEEN, SS_MAXED,
+  SS_W,      // bits of the current labels
+  SS_FOK,    // filter rounds allowed (cleared once one lists most of the DFA's states)
+  SS_NDUP,   // states listed by the current filter round
+  SS_WORDS
+};
 
 struct BatchArgs {
   const SegInfo *segs;
@@ -65,6 +72,14 @@ struct BatchArgs {
   uint32_t *tmp;           // total_states (multi-stage plans)
   u128 *table;
   uint32_t *bm[2];         // direct rounds: one bit per table slot (ping-pong)
+  uint32_t *seen1, *seen2; // filter rounds: 2-bit counters over 2^mbits buckets (all DFAs)
+  uint32_t *seen3, *seen4; // second filter, 2^(mbits-1) buckets
+  uint32_t *tmp2;          // total_states: second-filter bucket
+  uint32_t mbits;
+  unsigned long long *rep; // total_slots: filter rounds' (round, ~smallest local state) per slot
+  uint32_t *dups, *dups2, *dups3;   // per-warp lists: global state, second bucket, DFA
+  uint32_t *wcnt;          // per-warp list lengths
+  uint32_t dup_cap;        // list capacity per warp
   uint32_t *minrep;        // total_slots: smallest member per label (canonical numbering)
   uint32_t *tile_cnt;      // ntiles: first members per tile (canonical numbering)
   uint32_t *tile_pre;      // ntiles: their exclusive prefix sums
@@ -79,10 +94,179 @@ struct BatchArgs {
   unsigned long long timeout_ns, barrier_ns;
 };
 
-// A DFA's round is direct when its whole signature, (k+1) labels of w bits,
-// fits in log2S bits: the packed signature is then the new label itself.
-__device__ __forceinline__ bool batch_direct(const SegInfo &S, uint32_t w) {
-  return (uint64_t)(S.k + 1) * w <= S.log2S;
+enum : uint32_t { BM_DIRECT = 0, BM_FILTER = 1, BM_TABLE = 2 };
+
+// Mode of a DFA's round r (w = its words in the bookkeeping array, as they
+// stand before the round): direct when the packed signature fits in log2S
+// bits; filter when the previous round left at least n/64 blocks (most blocks
+// small) and the signature fits one exact key; otherwise table.
+__device__ __forceinline__ uint32_t batch_mode(const SegInfo &S, const uint32_t *w, uint32_t r) {
+  const uint32_t wd = w[SS_W];
+  if ((uint64_t)(S.k + 1) * wd <= S.log2S) return BM_DIRECT;
+  if (r > 1 && w[SS_FOK] && (uint64_t)w[SS_PREV] * 64 >= S.n && (uint64_t)(S.k + 1) * wd <= 125) return BM_FILTER;
+  return BM_TABLE;
+}
+
+// Filter round, pass A over one tile: hash every signature (the DFA's number
+// mixed in, so that equal local signatures of different DFAs spread apart)
+// into the 2-bit counters; keep the two buckets per state.
+__device__ __forceinline__ void batch_filter_a(const BatchArgs &A, const SegInfo &S, const Tile &T,
+                                              const uint32_t *__restrict__ src) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n = S.n, k = S.k;
+  const uint32_t *lsrc = src + S.state_off;
+  const unsigned long long keep = policy_evict_last();
+  for (uint32_t base = 0; base < T.len; base += 32) {
+    if (base + lane >= T.len) continue;
+    const uint32_t q = T.start + base + lane;
+    unsigned long long h = hash_step(0x243F6A8885A308D3ull ^ ((unsigned long long)T.seg * 0xD6E8FEB86659FD93ull),
+                                     lsrc[q]);
+    for (uint32_t a = 0; a < k; ++a) h = hash_step(h, ld_u32_hint(lsrc + S.delta[(size_t)a * n + q], keep));
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    const uint32_t b = (uint32_t)(h >> (64 - A.mbits));
+    const uint32_t bit = 1u << (b & 31u);
+    if (atomicOr(&A.seen1[b >> 5], bit) & bit) atomicOr(&A.seen2[b >> 5], bit);
+    A.tmp[S.state_off + q] = b;
+    unsigned long long h2 = (h ^ 0x9E3779B97F4A7C15ull) * 0xc4ceb9fe1a85ec53ull;
+    h2 ^= h2 >> 31;
+    A.tmp2[S.state_off + q] = (uint32_t)(h2 >> (64 - (A.mbits - 1)));
+  }
+}
+
+// Pass B over one tile: a state alone in its bucket keeps its local number as
+// label (a new singleton block); the others are listed (state, second bucket,
+// DFA) and enter the second filter.
+__device__ __forceinline__ void batch_filter_b(const BatchArgs &A, const SegInfo &S, const Tile &T,
+                                              uint32_t *__restrict__ dst, uint32_t r, uint32_t *list,
+                                              uint32_t *list2, uint32_t *list3, uint32_t &cursor) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t uniq = 0, listed = 0;
+  for (uint32_t base = 0; base < T.len; base += 32) {
+    const bool valid = base + lane < T.len;
+    const uint32_t q = T.start + base + lane, gq = S.state_off + q;
+    bool dup = false;
+    uint32_t b2 = 0;
+    if (valid) {
+      const uint32_t b = A.tmp[gq];
+      dup = (A.seen2[b >> 5] >> (b & 31u)) & 1u;
+      if (!dup) {
+        dst[gq] = q;
+        ++uniq;
+      } else {
+        b2 = A.tmp2[gq];
+        const uint32_t bit = 1u << (b2 & 31u);
+        if (atomicOr(&A.seen3[b2 >> 5], bit) & bit) atomicOr(&A.seen4[b2 >> 5], bit);
+      }
+    }
+    const unsigned dm = __ballot_sync(0xFFFFFFFFu, dup);
+    if (dup) {
+      const uint32_t p = cursor + __popc(dm & ((1u << lane) - 1u));
+      list[p] = gq;
+      list2[p] = b2;
+      list3[p] = T.seg;
+    }
+    cursor += __popc(dm);
+    listed += __popc(dm);
+  }
+  const uint32_t u = __reduce_add_sync(0xFFFFFFFFu, uniq);
+  if (lane == 0) {
+    if (u) atomicAdd(&A.cnt[T.seg * 3 + r % 3], u);
+    if (listed) atomicAdd(&A.ss[T.seg * SS_WORDS + SS_NDUP], listed);
+  }
+}
+
+// Adds one to DFA seg's count of new blocks for every lane with `hit`, one
+// atomic per (warp, DFA).
+__device__ __forceinline__ void count_per_dfa(const BatchArgs &A, bool valid, bool hit, uint32_t seg, uint32_t r) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const unsigned hm = __ballot_sync(0xFFFFFFFFu, valid && hit);
+  const unsigned grp = __match_any_sync(0xFFFFFFFFu, valid ? seg : 0xFFFFFFFFu) & __ballot_sync(0xFFFFFFFFu, valid);
+  if (valid && lane == (uint32_t)(__ffs(grp) - 1) && (grp & hm)) atomicAdd(&A.cnt[seg * 3 + r % 3], __popc(grp & hm));
+}
+
+// Pass F over the warp's list: a listed state alone in its second bucket is
+// unique too; the rest stay listed (compacted in place).
+__device__ __forceinline__ void batch_filter_f(const BatchArgs &A, uint32_t *__restrict__ dst, uint32_t r,
+                                              uint32_t *list, const uint32_t *list2, uint32_t *list3, uint32_t nd,
+                                              uint32_t &cursor_out) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t cursor = 0;
+  for (uint32_t base = 0; base < nd; base += 32) {
+    const uint32_t i = base + lane;
+    const bool valid = i < nd;
+    uint32_t gq = 0, seg = 0;
+    bool still = false;
+    if (valid) {
+      gq = list[i];
+      seg = list3[i];
+      const uint32_t b2 = list2[i];
+      still = (A.seen4[b2 >> 5] >> (b2 & 31u)) & 1u;
+      if (!still) dst[gq] = gq - A.segs[seg].state_off;
+    }
+    count_per_dfa(A, valid, !still, seg, r);
+    // every lane read its entry above: positions written below are <= the ones read
+    const unsigned sm = __ballot_sync(0xFFFFFFFFu, still);
+    if (still) {
+      const uint32_t p = cursor + __popc(sm & ((1u << lane) - 1u));
+      list[p] = gq;
+      list3[p] = seg;
+    }
+    cursor += __popc(sm);
+  }
+  cursor_out = cursor;
+}
+
+// Pass D over the warp's list: the listed states left insert their exact keys
+// into their own DFA's table region (lanes may hold different DFAs: each lane
+// inserts alone) and each slot keeps its smallest member (atomicMax on
+// (round, ~local state)).
+__device__ __forceinline__ void batch_filter_d(const BatchArgs &A, const uint32_t *__restrict__ src, uint32_t r,
+                                              uint32_t epoch, const uint32_t *list, const uint32_t *list3,
+                                              uint32_t nd) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const unsigned long long keep = policy_evict_last();
+  const unsigned long long etag = (unsigned long long)epoch << (64 - A.ebits);
+  for (uint32_t i = lane; i < nd; i += 32) {
+    const uint32_t gq = list[i];
+    const SegInfo &S = A.segs[list3[i]];
+    const uint32_t q = gq - S.state_off, w = A.ss[list3[i] * SS_WORDS + SS_W];
+    const uint32_t *lsrc = src + S.state_off;
+    u128 key[1] = {u128{0ull, 0ull}};
+    put_bits(key[0], lsrc[q], 0);
+    for (uint32_t a = 0; a < S.k; ++a) put_bits(key[0], ld_u32_hint(lsrc + S.delta[(size_t)a * S.n + q], keep), (a + 1) * w);
+    key[0].hi |= etag;
+    uint32_t slot[1] = {(uint32_t)(mix128(key[0]) >> 32) & table_mask(S.log2S)};
+    const bool want[1] = {true};
+    bool is_new[1];
+    table_insert_vec<1>(A.table + S.table_off, table_mask(S.log2S), key, A.ebits, epoch, want, slot, is_new,
+                        &A.ctrl->err);
+    A.tmp[gq] = slot[0];
+    atomicMax(&A.rep[S.table_off + slot[0]], ((unsigned long long)r << 32) | (unsigned long long)(~q));
+  }
+}
+
+// Pass C over the warp's list: the listed states take their slot's smallest
+// member as label; a state that is its slot's smallest member counts a block.
+__device__ __forceinline__ void batch_filter_c(const BatchArgs &A, uint32_t *__restrict__ dst, uint32_t r,
+                                              const uint32_t *list, const uint32_t *list3, uint32_t nd) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t base = 0; base < nd; base += 32) {
+    const uint32_t i = base + lane;
+    const bool valid = i < nd;
+    uint32_t seg = 0;
+    bool first = false;
+    if (valid) {
+      const uint32_t gq = list[i];
+      seg = list3[i];
+      const SegInfo &S = A.segs[seg];
+      const uint32_t m = ~(uint32_t)A.rep[S.table_off + A.tmp[gq]];
+      dst[gq] = m;
+      first = m == gq - S.state_off;
+    }
+    count_per_dfa(A, valid, first, seg, r);
+  }
 }
 
 // Direct round over one tile: new label = packed signature; a bitmap over the
@@ -310,7 +494,18 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
     A.ss[i * SS_WORDS + SS_ACTIVE] = 1u;
     A.ss[i * SS_WORDS + SS_FINAL] = 1u;
     A.ss[i * SS_WORDS + SS_W] = 1u;
+    A.ss[i * SS_WORDS + SS_FOK] = 1u;
   }
+  // filter counters and slot owners start clean
+  for (uint64_t i = tid; i < ((uint64_t)1 << A.mbits) / 32; i += stride) {
+    A.seen1[i] = 0u;
+    A.seen2[i] = 0u;
+  }
+  for (uint64_t i = tid; i < ((uint64_t)1 << A.mbits) / 64; i += stride) {
+    A.seen3[i] = 0u;
+    A.seen4[i] = 0u;
+  }
+  for (uint64_t i = tid; i < A.total_slots; i += stride) A.rep[i] = 0ull;
   // tile list: DFA i's tiles are tile_off[i] .. tile_off[i + 1) - 1, one warp per DFA
   for (uint32_t i = gwarp; i < A.nsegs; i += nwarps) {
     const uint32_t t0 = A.tile_off[i], nt = A.tile_off[i + 1] - t0, n = A.segs[i].n;
@@ -325,8 +520,12 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
     const bool round1 = r == 1;
     const uint32_t *src = A.lab[(r - 1) & 1];
     uint32_t *dst = A.lab[r & 1];
+    // some DFA takes a filter round (decided by the last bookkeeping)
+    const bool any_filter = !round1 && ld_relaxed(&C->flag2[r % 3]) != 0u;
+    if (leader) C->flag2[(r + 2) % 3] = 0u;
     // the bitmap of the next round starts clean (the one of the previous round is free now)
     for (uint64_t i = tid; i < bm_words; i += stride) A.bm[(r + 1) & 1][i] = 0u;
+    uint32_t epoch0 = 0;
     for (uint32_t s = 0; ok && s < A.max_stages; ++s) {
       if (epoch == emax) {
         for (uint64_t i = tid; i < A.total_slots; i += stride)
@@ -336,13 +535,19 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
         if (!ok) break;
       }
       ++epoch;
+      if (s == 0) epoch0 = epoch;
       cta_cache_clear(&cache);
       for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
         const Tile T = A.tiles[t];
         if (!ld_relaxed(&A.ss[T.seg * SS_WORDS + SS_ACTIVE])) continue;
         const SegInfo &S = A.segs[T.seg];
         const uint32_t w = A.ss[T.seg * SS_WORDS + SS_W];
-        if (batch_direct(S, w)) {
+        const uint32_t mode = batch_mode(S, A.ss + T.seg * SS_WORDS, r);
+        if (mode == BM_FILTER) {
+          if (s == 0) batch_filter_a(A, S, T, src);
+          continue;
+        }
+        if (mode == BM_DIRECT) {
           if (s != 0) continue;
           uint32_t *wbm = s_wbm[threadIdx.x >> 5];
           if (round1) batch_direct_tile<true>(A, S, T, w, src, dst, A.bm[r & 1], wbm, r);
@@ -356,21 +561,60 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
         else batch_table_tile<VEC, false>(A, S, T, P, s, last, epoch, src, dst, &cache, r);
       }
       ok = grid_sync(C, A.barrier_ns);
+      if (ok && s == 0 && any_filter) {
+        // filter passes B, F, D, C; each warp keeps its own list (and its length in a register)
+        const size_t at = (size_t)gwarp * A.dup_cap;
+        uint32_t *list = A.dups + at, *list2 = A.dups2 + at, *list3 = A.dups3 + at;
+        uint32_t nd = 0;
+        for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+          const Tile T = A.tiles[t];
+          if (!ld_relaxed(&A.ss[T.seg * SS_WORDS + SS_ACTIVE])) continue;
+          const SegInfo &S = A.segs[T.seg];
+          if (batch_mode(S, A.ss + T.seg * SS_WORDS, r) != BM_FILTER) continue;
+          batch_filter_b(A, S, T, dst, r, list, list2, list3, nd);
+        }
+        ok = grid_sync(C, A.barrier_ns);
+        if (ok) {
+          batch_filter_f(A, dst, r, list, list2, list3, nd, nd);
+          ok = grid_sync(C, A.barrier_ns);
+        }
+        if (ok) {
+          batch_filter_d(A, src, r, epoch0, list, list3, nd);
+          ok = grid_sync(C, A.barrier_ns);
+        }
+        if (ok) {
+          batch_filter_c(A, dst, r, list, list3, nd);
+          for (uint64_t i = tid; i < ((uint64_t)1 << A.mbits) / 32; i += stride) {
+            A.seen1[i] = 0u;
+            A.seen2[i] = 0u;
+          }
+          for (uint64_t i = tid; i < ((uint64_t)1 << A.mbits) / 64; i += stride) {
+            A.seen3[i] = 0u;
+            A.seen4[i] = 0u;
+          }
+          ok = grid_sync(C, A.barrier_ns);
+        }
+      }
     }
     if (!ok) break;
     // bookkeeping: one thread per DFA
-    uint32_t still = 0;
+    uint32_t still = 0, next_filter = 0;
     for (uint32_t i = tid; i < A.nsegs; i += stride) {
       uint32_t *w = A.ss + i * SS_WORDS;
       A.cnt[i * 3 + (r + 2) % 3] = 0u;
       if (!w[SS_ACTIVE]) continue;
       const SegInfo &S = A.segs[i];
+      const uint32_t mode = batch_mode(S, w, r);   // this round's mode (words not yet updated)
       const uint32_t B = A.cnt[i * 3 + r % 3];
       const uint32_t prev = round1 ? __popc(w[SS_SEEN]) : w[SS_PREV];
       w[SS_EXECUTED] = r;
       w[SS_FINAL] = r & 1;
       w[SS_B] = B;
-      w[SS_W] = batch_direct(S, w[SS_W]) ? (S.k + 1) * w[SS_W] : S.log2S;   // width of this round's labels
+      // width of this round's labels
+      w[SS_W] = mode == BM_DIRECT ? (S.k + 1) * w[SS_W] : mode == BM_FILTER ? S.wid : S.log2S;
+      // a filter round that listed most states (large blocks): later rounds use the table
+      if (mode == BM_FILTER && (uint64_t)w[SS_NDUP] * 2 > S.n) w[SS_FOK] = 0u;
+      w[SS_NDUP] = 0u;
       if (B == prev) {
         w[SS_ACTIVE] = 0u;               // fixpoint (Algorithm 4's until-test)
       } else {
@@ -383,11 +627,14 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
           w[SS_MAXED] = 1u;
         } else {
           ++still;
+          if (batch_mode(S, w, r + 1) == BM_FILTER) next_filter = 1u;
         }
       }
     }
     const uint32_t bs = block_sum(still, s_red);
     if (threadIdx.x == 0 && bs) atomicAdd(&C->cnt[r % 3], bs);
+    const uint32_t bf = block_sum(next_filter, s_red);
+    if (threadIdx.x == 0 && bf) atomicOr(&C->flag2[(r + 1) % 3], 1u);
     ok = grid_sync(C, A.barrier_ns);
     if (!ok) break;
     const uint32_t active = ld_relaxed(&C->cnt[r % 3]);
@@ -496,12 +743,19 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
 // ------------------------------------------------------------------ host side
 
 struct BatchLayout {
-  size_t ctrl, segs, tile_off, tiles, lab0, lab1, tmp, table, bm0, bm1, minrep, tile_cnt, tile_pre, partials, out, cnt, ss, stage,
-      total;
+  size_t ctrl, segs, tile_off, tiles, lab0, lab1, tmp, tmp2, seen1, seen2, seen3, seen4, rep, dups, dups2, dups3, table,
+      bm0, bm1, minrep, tile_cnt, tile_pre, partials, out, cnt, ss, stage, total;
+  size_t list_entries;
+  uint32_t mbits;
   uint64_t total_states, total_slots;
   uint32_t ntiles, max_stages, ebits;
   size_t stage_bytes;
 };
+
+// Warps of the batch kernel's cooperative grid (the larger of the two
+// schedules' grids); without a visible device, the largest grid the launcher
+// accepts.
+static size_t batch_max_warps();
 
 // Where the inputs of a batch live: host[2i] / host[2i + 1] tell whether DFA
 // i's delta / accept are host memory, to be staged into the workspace.  With
@@ -543,20 +797,20 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchIn
     s.k = d.k;
     s.state_off = (uint32_t)st;
     s.log2S = ceil_log2((uint64_t)d.n * 2 < 64 ? 64 : (uint64_t)d.n * 2);
+    s.wid = ceil_log2(d.n) > 0 ? ceil_log2(d.n) : 1;
     s.table_off = sl;
     // label widths a DFA goes through: 1 bit, then (k+1) times wider while the
-    // rounds are direct, then log2S bits (table rounds) for good; the table
-    // rounds' plans decide the stage count and the epoch bits left free
+    // rounds are direct; then log2S bits after a table round or wid bits after
+    // a filter round.  The plans of the table and filter rounds decide the
+    // stage count and the epoch bits left free.
     if (d.k > 0) {
       uint64_t w = 1;
       while ((uint64_t)(d.k + 1) * w <= s.log2S) w *= d.k + 1;   // direct rounds
-      for (;;) {
-        const StagePlan p = make_plan(d.k, (uint32_t)w, s.log2S);
+      for (const uint64_t x : {w, (uint64_t)s.log2S, (uint64_t)s.wid}) {
+        const StagePlan p = make_plan(d.k, (uint32_t)x, s.log2S);
         max_stages = std::max(max_stages, p.stages);
         ebits = std::min(ebits, p.ebits);
         multi |= p.stages > 1;
-        if (w == s.log2S) break;
-        w = s.log2S;
       }
     }
     if (tile_off_out) tile_off_out->push_back(ntiles);
@@ -600,7 +854,19 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchIn
   L.tiles = take((size_t)ntiles * sizeof(Tile));
   L.lab0 = take(st * 4);
   L.lab1 = take(st * 4);
-  L.tmp = multi ? take(st * 4) : SIZE_MAX;
+  (void)multi;
+  L.tmp = take(st * 4);   // multi-stage slots; filter buckets and slots
+  L.tmp2 = take(st * 4);
+  L.mbits = std::min<uint32_t>(31, std::max<uint32_t>(12, ceil_log2(st) + 2));
+  L.seen1 = take(((size_t)1 << L.mbits) / 8);
+  L.seen2 = take(((size_t)1 << L.mbits) / 8);
+  L.seen3 = take(((size_t)1 << L.mbits) / 16);
+  L.seen4 = take(((size_t)1 << L.mbits) / 16);
+  L.rep = take(sl * 8);
+  L.list_entries = ((size_t)ntiles + batch_max_warps()) * kTile;
+  L.dups = take(L.list_entries * 4);
+  L.dups2 = take(L.list_entries * 4);
+  L.dups3 = take(L.list_entries * 4);
   L.table = take(sl * 16);
   L.bm0 = take((sl + 31) / 32 * 4);
   L.bm1 = take((sl + 31) / 32 * 4);
@@ -619,6 +885,25 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchIn
 
 static const void *batch_kernel_for(uint32_t vec) {
   return vec == 2 ? (const void *)batch_kernel<2> : (const void *)batch_kernel<1>;
+}
+
+static size_t batch_max_warps() {
+  const size_t fallback = kMaxGridB * (kBatchThreads / 32);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fallback;
+  }
+  size_t best = 0;
+  for (uint32_t v : {1u, 2u}) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_for(v), kBatchThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return fallback;
+    }
+    best = std::max(best, (size_t)sms * (size_t)(per_sm < 1 ? 1 : per_sm) * (kBatchThreads / 32));
+  }
+  return best;
 }
 
 // Launches the batch kernel as a CUDA graph: the control-block reset and the
@@ -804,7 +1089,17 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
   a.total_slots = L.total_slots;
   a.lab[0] = reinterpret_cast<uint32_t *>(ws + L.lab0);
   a.lab[1] = reinterpret_cast<uint32_t *>(ws + L.lab1);
-  a.tmp = L.tmp == SIZE_MAX ? nullptr : reinterpret_cast<uint32_t *>(ws + L.tmp);
+  a.tmp = reinterpret_cast<uint32_t *>(ws + L.tmp);
+  a.tmp2 = reinterpret_cast<uint32_t *>(ws + L.tmp2);
+  a.mbits = L.mbits;
+  a.seen1 = reinterpret_cast<uint32_t *>(ws + L.seen1);
+  a.seen2 = reinterpret_cast<uint32_t *>(ws + L.seen2);
+  a.seen3 = reinterpret_cast<uint32_t *>(ws + L.seen3);
+  a.seen4 = reinterpret_cast<uint32_t *>(ws + L.seen4);
+  a.rep = reinterpret_cast<unsigned long long *>(ws + L.rep);
+  a.dups = reinterpret_cast<uint32_t *>(ws + L.dups);
+  a.dups2 = reinterpret_cast<uint32_t *>(ws + L.dups2);
+  a.dups3 = reinterpret_cast<uint32_t *>(ws + L.dups3);
   a.table = reinterpret_cast<u128 *>(ws + L.table);
   a.bm[0] = reinterpret_cast<uint32_t *>(ws + L.bm0);
   a.bm[1] = reinterpret_cast<uint32_t *>(ws + L.bm1);
@@ -832,6 +1127,10 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
     return cuda_fail(e, "occupancy");
   const int grid = sms * (per_sm < 1 ? 1 : per_sm);
   if ((size_t)grid > kMaxGridB) return fail(DFA_ECUDA, "grid too large");
+  // list capacity per warp: the states of the warp's tiles (tiles t = warp + j * nwarps)
+  const size_t nwarps = (size_t)grid * (kBatchThreads / 32);
+  if (nwarps > batch_max_warps()) return fail(DFA_ECUDA, "grid larger than the workspace was sized for");
+  a.dup_cap = (uint32_t)(((size_t)L.ntiles + nwarps - 1) / nwarps * kTile);
   e = launch_batch_graph(a, grid, st);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch of the batch kernel");
   Ctrl c{};

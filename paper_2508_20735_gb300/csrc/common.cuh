@@ -223,6 +223,13 @@ __device__ __forceinline__ unsigned long long mix128(u128 k) {
   return h;
 }
 
+// One step of the signature hash of filter rounds (a multiply-xorshift over
+// the components; any hash will do: uniqueness is proved by counting).
+__device__ __forceinline__ unsigned long long hash_step(unsigned long long h, uint32_t c) {
+  h = (h ^ c) * 0x9E3779B97F4A7C15ull;
+  return h ^ (h >> 29);
+}
+
 __device__ __forceinline__ uint32_t table_mask(uint32_t log2S) {
   return (log2S >= 32) ? 0xFFFFFFFFu : ((1u << log2S) - 1u);
 }

@@ -263,10 +263,6 @@ __device__ __forceinline__ u128 pack_key(const MooreArgs &A, uint32_t w, const u
 // one proves its signature unique whatever the hash, since equal signatures
 // hash alike; hash quality only affects how many unique signatures are sent
 // on to the exact table.
-__device__ __forceinline__ unsigned long long hash_step(unsigned long long h, uint32_t c) {
-  h = (h ^ c) * 0x9E3779B97F4A7C15ull;
-  return h ^ (h >> 29);
-}
 
 __device__ __forceinline__ void filter_pass_a(const MooreArgs &A, const uint32_t *__restrict__ src) {
   const uint32_t n = A.n, k = A.k;
