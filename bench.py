@@ -48,6 +48,10 @@ def parse():
                     help="profiling cases: 2^lg states instead of 2^24 (same k, seed and acceptance)")
     ap.add_argument("--stop-discrete", action="store_true",
                     help="profiling cases: time the call with DFA_FLAG_STOP_DISCRETE")
+    ap.add_argument("--case", default="headline", choices=["headline", "batch"],
+                    help="batch: time only the packed batched call on --batch-dfas DFAs of the batch recipe")
+    ap.add_argument("--batch-dfas", type=int, default=4096)
+    ap.add_argument("--schedule", type=int, default=-1, help="batch case: kernel schedule (-1 = autotuned)")
     args = ap.parse_args()
     if args.lg != 24:
         WORKLOAD.update(workload=f"random_dfa_n2^{args.lg}_k4", n=1 << args.lg)
@@ -274,11 +278,46 @@ def extras(g):
     return out
 
 
+def run_batch_case(args, local):
+    """The batched workload alone: one packed dfa_minimise_batch_packed call per
+    step over --batch-dfas DFAs of the batch recipe (n log-uniform in [64, 65536],
+    k in 2..8, acceptance 0.3, seed 4), inputs resident on the device."""
+    import torch
+
+    import dfagen
+    import paper_2508_20735_gb300 as g
+    torch.cuda.set_device(local)
+    g.build()
+    dfas = dfagen.batch_dfas(args.batch_dfas, 64, 65_536, 2, 8, 0.3, 4)
+    pn, pk, pd, pa = g.pack_batch([(X.delta, X.accept) for X in dfas])
+    out = torch.empty(int(pn.sum()), dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        g.minimise_batch_packed(pn, pk, pd, pa, out=out, schedule=args.schedule)
+    dev = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            dev.append(g.minimise_batch_packed(pn, pk, pd, pa, out=out, schedule=args.schedule)[1][0].device_ns)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+    print(json.dumps({"metric": "DFAs minimised/sec (batched)", "value": args.batch_dfas * args.steps / el,
+                      "unit": "DFAs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": el * 1e3 / args.steps, "device_ms": statistics.median(dev) / 1e6,
+                      "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+                      "config": {"workload": f"batch_{args.batch_dfas}_dfas", "states": int(pn.sum())},
+                      "clocks": clk.summary(), "gpu_launches": args.steps}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.case == "batch":
+        if rank == 0:
+            run_batch_case(args, local)
         return
     import numpy as np
     import torch
