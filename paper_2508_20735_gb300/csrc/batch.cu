@@ -79,7 +79,7 @@ struct BatchArgs {
   unsigned long long *rep; // total_slots: filter rounds' (round, ~smallest local state) per slot
   uint32_t *dups, *dups2, *dups3;   // per-warp lists: global state, second bucket, DFA
   uint32_t *wcnt;          // per-warp list lengths
-  uint32_t dup_cap;        // list capacity per warp
+  uint32_t dup_cap;        // list capacity per block
   uint32_t *minrep;        // total_slots: smallest member per label (canonical numbering)
   uint32_t *tile_cnt;      // ntiles: first members per tile (canonical numbering)
   uint32_t *tile_pre;      // ntiles: their exclusive prefix sums
@@ -93,6 +93,25 @@ struct BatchArgs {
   uint32_t vec;            // states per lane within a tile pass: 1 or 2
   unsigned long long timeout_ns, barrier_ns;
 };
+
+// Tiles of a pass are dealt per block: block b takes tiles b, b + grid, b +
+// 2 grid, ... in order (so that the grid sweeps the batch front to back, with
+// the tables of neighbouring DFAs in L2 together) and its warps take the next
+// of them from a shared counter, so that costly tiles do not hold up a warp
+// while its neighbours idle.  The counter is reset (start_tiles) after a
+// barrier, before every pass.
+__device__ __forceinline__ uint32_t next_tile(const BatchArgs &A, uint32_t *s_next) {
+  uint32_t i = 0;
+  if ((threadIdx.x & 31u) == 0) i = atomicAdd(s_next, 1u);
+  i = __shfl_sync(0xFFFFFFFFu, i, 0);
+  const uint64_t t = (uint64_t)blockIdx.x + (uint64_t)i * gridDim.x;
+  return t < A.ntiles ? (uint32_t)t : A.ntiles;
+}
+
+__device__ __forceinline__ void start_tiles(uint32_t *s_next) {
+  if (threadIdx.x == 0) *s_next = 0u;
+  __syncthreads();
+}
 
 enum : uint32_t { BM_DIRECT = 0, BM_FILTER = 1, BM_TABLE = 2 };
 
@@ -136,11 +155,12 @@ __device__ __forceinline__ void batch_filter_a(const BatchArgs &A, const SegInfo
 }
 
 // Pass B over one tile: a state alone in its bucket keeps its local number as
-// label (a new singleton block); the others are listed (state, second bucket,
-// DFA) and enter the second filter.
+// label (a new singleton block); the others are listed in the block's list
+// (state, second bucket, DFA; slots taken from a shared cursor) and enter the
+// second filter.
 __device__ __forceinline__ void batch_filter_b(const BatchArgs &A, const SegInfo &S, const Tile &T,
                                               uint32_t *__restrict__ dst, uint32_t r, uint32_t *list,
-                                              uint32_t *list2, uint32_t *list3, uint32_t &cursor) {
+                                              uint32_t *list2, uint32_t *list3, uint32_t *s_cursor) {
   const uint32_t lane = threadIdx.x & 31u;
   uint32_t uniq = 0, listed = 0;
   for (uint32_t base = 0; base < T.len; base += 32) {
@@ -161,13 +181,17 @@ __device__ __forceinline__ void batch_filter_b(const BatchArgs &A, const SegInfo
       }
     }
     const unsigned dm = __ballot_sync(0xFFFFFFFFu, dup);
-    if (dup) {
-      const uint32_t p = cursor + __popc(dm & ((1u << lane) - 1u));
-      list[p] = gq;
-      list2[p] = b2;
-      list3[p] = T.seg;
+    if (dm) {
+      uint32_t at = 0;
+      if (lane == 0) at = atomicAdd(s_cursor, (uint32_t)__popc(dm));
+      at = __shfl_sync(0xFFFFFFFFu, at, 0);
+      if (dup) {
+        const uint32_t p = at + __popc(dm & ((1u << lane) - 1u));
+        list[p] = gq;
+        list2[p] = b2;
+        list3[p] = T.seg;
+      }
     }
-    cursor += __popc(dm);
     listed += __popc(dm);
   }
   const uint32_t u = __reduce_add_sync(0xFFFFFFFFu, uniq);
@@ -186,49 +210,45 @@ __device__ __forceinline__ void count_per_dfa(const BatchArgs &A, bool valid, bo
   if (valid && lane == (uint32_t)(__ffs(grp) - 1) && (grp & hm)) atomicAdd(&A.cnt[seg * 3 + r % 3], __popc(grp & hm));
 }
 
-// Pass F over the warp's list: a listed state alone in its second bucket is
-// unique too; the rest stay listed (compacted in place).
+// Listed entries resolved by the second filter are marked in their DFA word.
+static constexpr uint32_t kResolved = 0x80000000u;
+
+// Pass F over the block's list (warps take 32-entry chunks): a listed state
+// alone in its second bucket is unique too and is marked resolved.
 __device__ __forceinline__ void batch_filter_f(const BatchArgs &A, uint32_t *__restrict__ dst, uint32_t r,
-                                              uint32_t *list, const uint32_t *list2, uint32_t *list3, uint32_t nd,
-                                              uint32_t &cursor_out) {
-  const uint32_t lane = threadIdx.x & 31u;
-  uint32_t cursor = 0;
-  for (uint32_t base = 0; base < nd; base += 32) {
+                                              const uint32_t *list, const uint32_t *list2, uint32_t *list3,
+                                              uint32_t nd) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint32_t base = warp * 32; base < nd; base += nw * 32) {
     const uint32_t i = base + lane;
     const bool valid = i < nd;
-    uint32_t gq = 0, seg = 0;
+    uint32_t seg = 0;
     bool still = false;
     if (valid) {
-      gq = list[i];
+      const uint32_t gq = list[i];
       seg = list3[i];
       const uint32_t b2 = list2[i];
       still = (A.seen4[b2 >> 5] >> (b2 & 31u)) & 1u;
-      if (!still) dst[gq] = gq - A.segs[seg].state_off;
+      if (!still) {
+        dst[gq] = gq - A.segs[seg].state_off;
+        list3[i] = seg | kResolved;
+      }
     }
     count_per_dfa(A, valid, !still, seg, r);
-    // every lane read its entry above: positions written below are <= the ones read
-    const unsigned sm = __ballot_sync(0xFFFFFFFFu, still);
-    if (still) {
-      const uint32_t p = cursor + __popc(sm & ((1u << lane) - 1u));
-      list[p] = gq;
-      list3[p] = seg;
-    }
-    cursor += __popc(sm);
   }
-  cursor_out = cursor;
 }
 
-// Pass D over the warp's list: the listed states left insert their exact keys
-// into their own DFA's table region (lanes may hold different DFAs: each lane
-// inserts alone) and each slot keeps its smallest member (atomicMax on
+// Pass D over the block's list: the listed states left insert their exact
+// keys into their own DFA's table region (lanes may hold different DFAs: each
+// lane inserts alone) and each slot keeps its smallest member (atomicMax on
 // (round, ~local state)).
 __device__ __forceinline__ void batch_filter_d(const BatchArgs &A, const uint32_t *__restrict__ src, uint32_t r,
                                               uint32_t epoch, const uint32_t *list, const uint32_t *list3,
                                               uint32_t nd) {
-  const uint32_t lane = threadIdx.x & 31u;
   const unsigned long long keep = policy_evict_last();
   const unsigned long long etag = (unsigned long long)epoch << (64 - A.ebits);
-  for (uint32_t i = lane; i < nd; i += 32) {
+  for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) {
+    if (list3[i] & kResolved) continue;
     const uint32_t gq = list[i];
     const SegInfo &S = A.segs[list3[i]];
     const uint32_t q = gq - S.state_off, w = A.ss[list3[i] * SS_WORDS + SS_W];
@@ -247,14 +267,15 @@ __device__ __forceinline__ void batch_filter_d(const BatchArgs &A, const uint32_
   }
 }
 
-// Pass C over the warp's list: the listed states take their slot's smallest
-// member as label; a state that is its slot's smallest member counts a block.
+// Pass C over the block's list: the listed states left take their slot's
+// smallest member as label; a state that is its slot's smallest member counts
+// a block.
 __device__ __forceinline__ void batch_filter_c(const BatchArgs &A, uint32_t *__restrict__ dst, uint32_t r,
                                               const uint32_t *list, const uint32_t *list3, uint32_t nd) {
-  const uint32_t lane = threadIdx.x & 31u;
-  for (uint32_t base = 0; base < nd; base += 32) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint32_t base = warp * 32; base < nd; base += nw * 32) {
     const uint32_t i = base + lane;
-    const bool valid = i < nd;
+    const bool valid = i < nd && !(list3[i] & kResolved);
     uint32_t seg = 0;
     bool first = false;
     if (valid) {
@@ -476,6 +497,7 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
   __shared__ uint32_t s_red[kBatchThreads / 32];
   __shared__ CtaCache cache;
   __shared__ uint32_t s_wbm[kBatchThreads / 32][32];
+  __shared__ uint32_t s_next, s_cursor;   // next tile of the block; length of the block's list
   Ctrl *C = A.ctrl;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
@@ -537,7 +559,8 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
       ++epoch;
       if (s == 0) epoch0 = epoch;
       cta_cache_clear(&cache);
-      for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+      start_tiles(&s_next);
+      for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
         const Tile T = A.tiles[t];
         if (!ld_relaxed(&A.ss[T.seg * SS_WORDS + SS_ACTIVE])) continue;
         const SegInfo &S = A.segs[T.seg];
@@ -562,20 +585,22 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
       }
       ok = grid_sync(C, A.barrier_ns);
       if (ok && s == 0 && any_filter) {
-        // filter passes B, F, D, C; each warp keeps its own list (and its length in a register)
-        const size_t at = (size_t)gwarp * A.dup_cap;
+        // filter passes B, F, D, C over the block's own list
+        const size_t at = (size_t)blockIdx.x * A.dup_cap;
         uint32_t *list = A.dups + at, *list2 = A.dups2 + at, *list3 = A.dups3 + at;
-        uint32_t nd = 0;
-        for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+        if (threadIdx.x == 0) s_cursor = 0u;
+        start_tiles(&s_next);
+        for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
           const Tile T = A.tiles[t];
           if (!ld_relaxed(&A.ss[T.seg * SS_WORDS + SS_ACTIVE])) continue;
           const SegInfo &S = A.segs[T.seg];
           if (batch_mode(S, A.ss + T.seg * SS_WORDS, r) != BM_FILTER) continue;
-          batch_filter_b(A, S, T, dst, r, list, list2, list3, nd);
+          batch_filter_b(A, S, T, dst, r, list, list2, list3, &s_cursor);
         }
         ok = grid_sync(C, A.barrier_ns);
+        const uint32_t nd = s_cursor;   // the block's list length (read after the barrier)
         if (ok) {
-          batch_filter_f(A, dst, r, list, list2, list3, nd, nd);
+          batch_filter_f(A, dst, r, list, list2, list3, nd);
           ok = grid_sync(C, A.barrier_ns);
         }
         if (ok) {
@@ -648,7 +673,8 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
   // at table_off), count first members per tile, and rank them by a scan over
   // the tiles.
   if (ok) {
-    for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+    start_tiles(&s_next);
+    for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
       if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
@@ -661,7 +687,8 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
     ok = grid_sync(C, A.barrier_ns);
   }
   if (ok) {
-    for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+    start_tiles(&s_next);
+    for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
       if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
@@ -678,7 +705,8 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
     ok = grid_sync(C, A.barrier_ns);
   }
   if (ok) {
-    for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+    start_tiles(&s_next);
+    for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
       uint32_t c = T.len;
@@ -698,7 +726,8 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
   if (ok) ok = grid_excl_scan(A.tile_cnt, A.tile_pre, A.ntiles, A.partials, C, A.barrier_ns, s_red);
   if (ok) ok = grid_sync(C, A.barrier_ns);
   if (ok) {
-    for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+    start_tiles(&s_next);
+    for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
       uint32_t *o = A.out + S.state_off;
@@ -723,7 +752,8 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
     ok = grid_sync(C, A.barrier_ns);
   }
   if (ok) {
-    for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+    start_tiles(&s_next);
+    for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
       if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
@@ -863,7 +893,7 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchIn
   L.seen3 = take(((size_t)1 << L.mbits) / 16);
   L.seen4 = take(((size_t)1 << L.mbits) / 16);
   L.rep = take(sl * 8);
-  L.list_entries = ((size_t)ntiles + batch_max_warps()) * kTile;
+  L.list_entries = ((size_t)ntiles + batch_max_warps() / (kBatchThreads / 32)) * kTile;   // per block: its tiles
   L.dups = take(L.list_entries * 4);
   L.dups2 = take(L.list_entries * 4);
   L.dups3 = take(L.list_entries * 4);
@@ -1127,10 +1157,10 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
     return cuda_fail(e, "occupancy");
   const int grid = sms * (per_sm < 1 ? 1 : per_sm);
   if ((size_t)grid > kMaxGridB) return fail(DFA_ECUDA, "grid too large");
-  // list capacity per warp: the states of the warp's tiles (tiles t = warp + j * nwarps)
-  const size_t nwarps = (size_t)grid * (kBatchThreads / 32);
-  if (nwarps > batch_max_warps()) return fail(DFA_ECUDA, "grid larger than the workspace was sized for");
-  a.dup_cap = (uint32_t)(((size_t)L.ntiles + nwarps - 1) / nwarps * kTile);
+  // list capacity per block: the states of the block's tiles (tiles t = block + j * grid)
+  if ((size_t)grid * (kBatchThreads / 32) > batch_max_warps())
+    return fail(DFA_ECUDA, "grid larger than the workspace was sized for");
+  a.dup_cap = (uint32_t)(((size_t)L.ntiles + grid - 1) / grid * kTile);
   e = launch_batch_graph(a, grid, st);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch of the batch kernel");
   Ctrl c{};
