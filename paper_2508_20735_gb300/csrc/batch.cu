@@ -118,11 +118,11 @@ enum : uint32_t { BM_DIRECT = 0, BM_FILTER = 1, BM_TABLE = 2 };
 // Mode of a DFA's round r (w = its words in the bookkeeping array, as they
 // stand before the round): direct when the packed signature fits in log2S
 // bits; filter when the previous round left at least n/64 blocks (most blocks
-// small) and the signature fits one exact key; otherwise table.
+// small); otherwise table.
 __device__ __forceinline__ uint32_t batch_mode(const SegInfo &S, const uint32_t *w, uint32_t r) {
   const uint32_t wd = w[SS_W];
   if ((uint64_t)(S.k + 1) * wd <= S.log2S) return BM_DIRECT;
-  if (r > 1 && w[SS_FOK] && (uint64_t)w[SS_PREV] * 64 >= S.n && (uint64_t)(S.k + 1) * wd <= 125) return BM_FILTER;
+  if (r > 1 && w[SS_FOK] && (uint64_t)w[SS_PREV] * 64 >= S.n) return BM_FILTER;
   return BM_TABLE;
 }
 
@@ -240,28 +240,44 @@ __device__ __forceinline__ void batch_filter_f(const BatchArgs &A, uint32_t *__r
 
 // Pass D over the block's list: the listed states left insert their exact
 // keys into their own DFA's table region (lanes may hold different DFAs: each
-// lane inserts alone) and each slot keeps its smallest member (atomicMax on
-// (round, ~local state)).
+// lane inserts alone), in as many stages as the DFA's plan has (stage s tagged
+// with epoch epoch0 + s, the epoch of the round's table stage s; other DFAs'
+// table stages use other regions), and each final slot keeps its smallest
+// member (atomicMax on (round, ~local state)).
 __device__ __forceinline__ void batch_filter_d(const BatchArgs &A, const uint32_t *__restrict__ src, uint32_t r,
-                                              uint32_t epoch, const uint32_t *list, const uint32_t *list3,
+                                              uint32_t epoch0, const uint32_t *list, const uint32_t *list3,
                                               uint32_t nd) {
   const unsigned long long keep = policy_evict_last();
-  const unsigned long long etag = (unsigned long long)epoch << (64 - A.ebits);
   for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) {
     if (list3[i] & kResolved) continue;
     const uint32_t gq = list[i];
     const SegInfo &S = A.segs[list3[i]];
     const uint32_t q = gq - S.state_off, w = A.ss[list3[i] * SS_WORDS + SS_W];
     const uint32_t *lsrc = src + S.state_off;
-    u128 key[1] = {u128{0ull, 0ull}};
-    put_bits(key[0], lsrc[q], 0);
-    for (uint32_t a = 0; a < S.k; ++a) put_bits(key[0], ld_u32_hint(lsrc + S.delta[(size_t)a * S.n + q], keep), (a + 1) * w);
-    key[0].hi |= etag;
-    uint32_t slot[1] = {(uint32_t)(mix128(key[0]) >> 32) & table_mask(S.log2S)};
-    const bool want[1] = {true};
-    bool is_new[1];
-    table_insert_vec<1>(A.table + S.table_off, table_mask(S.log2S), key, A.ebits, epoch, want, slot, is_new,
-                        &A.ctrl->err);
+    const StagePlan P = make_plan(S.k, w, S.log2S);
+    const uint32_t total = S.k + 1, mask = table_mask(S.log2S);
+    uint32_t slot[1] = {0u};
+    for (uint32_t st = 0; st < P.stages; ++st) {
+      u128 key[1] = {u128{0ull, 0ull}};
+      uint32_t shift = 0, cbeg, cend;
+      if (st == 0) {
+        cbeg = 0;
+        cend = P.first < total ? P.first : total;
+      } else {
+        put_bits(key[0], slot[0], 0);
+        shift = P.carry;
+        cbeg = P.first + (st - 1) * P.per;
+        cend = cbeg + P.per < total ? cbeg + P.per : total;
+      }
+      for (uint32_t j = cbeg; j < cend; ++j, shift += w)
+        put_bits(key[0], j == 0 ? lsrc[q] : ld_u32_hint(lsrc + S.delta[(size_t)(j - 1) * S.n + q], keep), shift);
+      const uint32_t ep = epoch0 + st;
+      key[0].hi |= (unsigned long long)ep << (64 - A.ebits);
+      slot[0] = (uint32_t)(mix128(key[0]) >> 32) & mask;
+      const bool want[1] = {true};
+      bool is_new[1];
+      table_insert_vec<1>(A.table + S.table_off, mask, key, A.ebits, ep, want, slot, is_new, &A.ctrl->err);
+    }
     A.tmp[gq] = slot[0];
     atomicMax(&A.rep[S.table_off + slot[0]], ((unsigned long long)r << 32) | (unsigned long long)(~q));
   }
@@ -549,7 +565,9 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
     for (uint64_t i = tid; i < bm_words; i += stride) A.bm[(r + 1) & 1][i] = 0u;
     uint32_t epoch0 = 0;
     for (uint32_t s = 0; ok && s < A.max_stages; ++s) {
-      if (epoch == emax) {
+      // a round's stages (and its filter inserts) take epochs epoch0 .. epoch0 + max_stages - 1:
+      // wrap before stage 0 unless they all fit
+      if (s == 0 ? (uint64_t)epoch + A.max_stages > emax : epoch == emax) {
         for (uint64_t i = tid; i < A.total_slots; i += stride)
           reinterpret_cast<uint4 *>(A.table)[i] = make_uint4(0, 0, 0, 0);
         ok = grid_sync(C, A.barrier_ns);
