@@ -140,6 +140,22 @@ def whole_job(units: float, elapsed_s: float, dist=None, device="cpu"):
     return float(u.item()) / float(t.item()), float(t.item())
 
 
+def host_info():
+    """Host core count and CPU model (recorded beside the CPU baseline)."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":", 1)[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
 def cpu_baseline(A, seconds_hint=True):
     """The oracle as it stands, one Moore round on the full workload (a bounded sample)."""
     import numpy as np
@@ -149,7 +165,7 @@ def cpu_baseline(A, seconds_hint=True):
     oracle.moore_round(A.delta, block)
     dt = time.perf_counter() - t
     n, k = A.n, A.k
-    return {"value": n * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
             "sample": f"one signature-refinement round of the numpy oracle on the full {n}-state, {k}-letter DFA "
                       f"({dt:.1f} s)"}
 
@@ -270,7 +286,16 @@ def extras(g):
             st, _, eq, _ = srv.wait(t)
             wrong += int(bool(eq) != pool[i % len(pool)][2])
         s = srv.stats()
+    # the same requests one after another through dfa_equivalent (host inputs, as submitted to the server)
+    for A, B, _ in pool:
+        g.equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start))
+    t0 = time.perf_counter()
+    for i in range(2 * len(pool)):
+        A, B, _ = pool[i % len(pool)]
+        g.equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start))
+    serial = 2 * len(pool) / (time.perf_counter() - t0)
     out["serve_equiv"] = {"requests": nreq, "distinct_pairs": len(pool), "closed_loop_rps": cap,
+                          "serial_dfa_equivalent_rps": serial, "closed_loop_vs_serial": cap / serial,
                           "offered_rps": lam, "p50_us": s["p50_us"], "p99_us": s["p99_us"],
                           "throughput_rps": s["throughput_rps"], "wrong_verdicts": wrong,
                           "sample": "Poisson arrivals at 0.8 x closed-loop capacity; pairs of the served-equivalence "
@@ -414,6 +439,20 @@ def main():
                          "transitions_per_s": n * k * sr.rounds_executed / sd_s,
                          "plain_device_ms": statistics.median(dev_ns) * 1e-6}
 
+    # the ceiling of the label gathers: random 4-byte L2 reads, measured now on a 64 MiB (L2-resident) array;
+    # each round issues (k + 1) n such requests (k label gathers, one renumbering atomic per state)
+    l2 = None
+    try:
+        probe = torch.zeros(1 << 24, dtype=torch.int32, device="cuda")
+        peak_l2 = g.probe_l2_gather(probe, 1 << 28, stream=stream)
+        del probe
+        req = (k + 1) * n * statistics.mean(rounds)
+        l2 = {"bound": "l2_random_requests", "achieved": req / kernel_s / 1e9, "peak": peak_l2 / 1e9,
+              "unit": "G requests/s", "frac": req / kernel_s / peak_l2,
+              "requests_per_launch": req, "peak_source": "dfa_probe_l2_gather, measured in this run (64 MiB array)"}
+    except Exception as exc:   # a measurement aid: report why it is missing
+        l2 = {"unavailable": str(exc)}
+
     # end to end through the same C call with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -462,7 +501,7 @@ def main():
                                l2="inputs larger than L2 (delta 256 MiB)",
                                parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps,
-                "roofline": roofline, "cpu_baseline": cpu, "extras": ex}
+                "roofline": roofline, "l2_roofline": l2, "cpu_baseline": cpu, "extras": ex}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -230,6 +230,20 @@ int dfa_minimise_noalloc(const dfa_t *dfa, const dfa_opts *opts, uint32_t *block
 /* ---------------------------------------------------------------- misc */
 
 /* Thread-local message describing the last failing call on this thread. */
+/* ---------------------------------------------------------------- measurement aid */
+
+/* Rate of random 4-byte reads from an array small enough to stay in L2: the
+ * ceiling of the label gathers of every refinement round (k n reads with no
+ * pattern per round, one L2 request each).  No counterpart in the paper.
+ *   table        device memory of table_bytes (a power of two >= 8; 64 MiB
+ *                matches the 2^24-state label array); read only, caller-owned;
+ *   reads        reads to time (rounded up to a whole number per thread);
+ *   stream       stream to run on (NULL = legacy default stream);
+ *   reads_per_s  out: reads per second of the timed pass (one untimed pass
+ *                first brings the table into L2).
+ * Synchronises the stream.  DFA_EINVAL for a bad size or a host pointer. */
+int dfa_probe_l2_gather(void *table, size_t table_bytes, uint64_t reads, void *stream, double *reads_per_s);
+
 const char *dfa_last_error(void);
 
 /* Library version string. */

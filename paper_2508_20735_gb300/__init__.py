@@ -80,6 +80,7 @@ _SIGS = [
     ("dfa_serve_stats", c_int, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
     ("dfa_serve_destroy", c_int, [c_void_p]),
     ("dfa_minimise_noalloc", c_int, [POINTER(DfaT), POINTER(DfaOpts), c_void_p, POINTER(DfaResult), c_void_p]),
+    ("dfa_probe_l2_gather", c_int, [c_void_p, c_size_t, c_uint64, c_void_p, POINTER(c_double)]),
     ("dfa_last_error", ctypes.c_char_p, []),
     ("dfa_version", ctypes.c_char_p, []),
 ]
@@ -364,6 +365,17 @@ def minimise_batch_packed(n, k, delta, accept, algo="moore", max_rounds=0, timeo
     if check and st != DFA_OK:
         raise DfaError(st, last_error())
     return out, res
+
+
+def probe_l2_gather(table, reads: int = 1 << 28, stream=None) -> float:
+    """Random 4-byte reads per second from `table` (a device tensor whose byte
+    size is a power of two; 64 MiB stays in L2): dfa_probe_l2_gather."""
+    rate = c_double(0.0)
+    st = lib().dfa_probe_l2_gather(_ptr(table), int(table.numel() * table.element_size()), int(reads),
+                                   _stream(stream), ctypes.byref(rate))
+    if st != DFA_OK:
+        raise DfaError(st, last_error())
+    return rate.value
 
 
 def header_functions() -> list[str]:

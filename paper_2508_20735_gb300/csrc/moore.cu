@@ -264,30 +264,49 @@ __device__ __forceinline__ u128 pack_key(const MooreArgs &A, uint32_t w, const u
 // hash alike; hash quality only affects how many unique signatures are sent
 // on to the exact table.
 
+__device__ __forceinline__ void filter_one(const MooreArgs &A, uint32_t q, unsigned long long h,
+                                           unsigned long long keep, unsigned long long drop) {
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  const uint32_t b = (uint32_t)(h >> (64 - A.mbits));
+  const uint32_t bit = 1u << (b & 31u);
+  const uint32_t old = atom_or_hint(&A.seen1[b >> 5], bit, keep);
+  if (old & bit) red_or_hint(&A.seen2[b >> 5], bit, keep);
+  st_u32_hint(A.tmp + q, b, drop);
+  unsigned long long h2 = (h ^ 0x9E3779B97F4A7C15ull) * 0xc4ceb9fe1a85ec53ull;
+  h2 ^= h2 >> 31;
+  st_u32_hint(A.tmp2 + q, (uint32_t)(h2 >> (64 - (A.mbits - 1))), drop);
+}
+
 __device__ __forceinline__ void filter_pass_a(const MooreArgs &A, const uint32_t *__restrict__ src) {
   const uint32_t n = A.n, k = A.k;
   const unsigned long long keep = policy_evict_last(), drop = policy_evict_first();
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  for (uint32_t q = tid; q < n; q += stride) {
+  uint32_t q = tid;
+  for (; (uint64_t)q + stride < n; q += 2 * stride) {
+    const uint32_t q2 = q + stride;
+    unsigned long long h = hash_step(0x243F6A8885A308D3ull, src[q]);
+    unsigned long long g = hash_step(0x243F6A8885A308D3ull, src[q2]);
+    for (uint32_t a = 0; a < k; ++a) {
+      const uint32_t *row = A.delta + (size_t)a * n;
+      const uint32_t d = A.stream_delta ? ld_u32_stream(row + q, drop) : row[q];
+      const uint32_t d2 = A.stream_delta ? ld_u32_stream(row + q2, drop) : row[q2];
+      const uint32_t c = ld_u32_hint(src + d, keep), c2 = ld_u32_hint(src + d2, keep);
+      h = hash_step(h, c);
+      g = hash_step(g, c2);
+    }
+    filter_one(A, q, h, keep, drop);
+    filter_one(A, q2, g, keep, drop);
+  }
+  if (q < n) {
     unsigned long long h = hash_step(0x243F6A8885A308D3ull, src[q]);
     for (uint32_t a = 0; a < k; ++a) {
       const uint32_t *row = A.delta + (size_t)a * n;
       const uint32_t d = A.stream_delta ? ld_u32_stream(row + q, drop) : row[q];
       h = hash_step(h, ld_u32_hint(src + d, keep));
     }
-    h ^= h >> 33;
-    h *= 0xff51afd7ed558ccdull;
-    h ^= h >> 33;
-    const uint32_t b = (uint32_t)(h >> (64 - A.mbits));
-    const uint32_t bit = 1u << (b & 31u);
-    // counters stay in L2 beside the labels; the buckets are streamed out
-    const uint32_t old = atom_or_hint(&A.seen1[b >> 5], bit, keep);
-    if (old & bit) red_or_hint(&A.seen2[b >> 5], bit, keep);
-    st_u32_hint(A.tmp + q, b, drop);
-    // an independent bucket for the second filter (states listed by pass B)
-    unsigned long long h2 = (h ^ 0x9E3779B97F4A7C15ull) * 0xc4ceb9fe1a85ec53ull;
-    h2 ^= h2 >> 31;
-    st_u32_hint(A.tmp2 + q, (uint32_t)(h2 >> (64 - (A.mbits - 1))), drop);
+    filter_one(A, q, h, keep, drop);
   }
 }
 

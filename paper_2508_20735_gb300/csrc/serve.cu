@@ -38,23 +38,34 @@ static constexpr int kServeThreads = 512;
 static constexpr uint32_t kServeTile = 256;
 static constexpr size_t kServeMaxGrid = 8192;
 
+enum : uint32_t { SM_DIRECT = 0, SM_FILTER = 1, SM_TABLE = 2 };
+
+// One admitted request as a step sees it.  The host picks the round's mode
+// (as dfa_minimise does: direct while the packed signature fits in log2S
+// bits, filter once the previous round left at least n/64 blocks, table
+// otherwise) and the plan of its table or filter keys.
 struct ServeSeg {
   const uint32_t *delta;
   const uint8_t *accept;
   uint32_t n, k;
   uint32_t *lab[2];
-  uint32_t *tmp;
+  uint32_t *tmp, *tmp2;          // multi-stage slots; filter buckets and slots
+  uint32_t *list, *list2;        // filter: listed states and their second buckets, per tile slice
   u128 *table;
-  uint32_t log2S;
-  uint32_t ebits;
-  StagePlan plan1, planr;
-  uint32_t round;      // round this step executes (1-based)
-  uint32_t epoch0;     // epoch of stage 0 of this round
+  unsigned long long *rep;       // filter: (round, ~smallest state) per slot
+  uint32_t *bm[2];               // direct: one bit per possible label (ping-pong)
+  uint32_t log2S, wid, ebits;
+  uint32_t mode, w;              // this round's mode; bits of the labels it reads
+  StagePlan plan;                // plan of the table or filter keys, (w, log2S)
+  uint32_t round;                // round this step executes (1-based)
+  uint32_t epoch0;               // epoch of stage 0 of this round
+  uint32_t tile0, ntiles;        // this request's tiles in the step's tile list
+  const uint32_t *err;           // nonzero if the request's targets failed validation: skip it
   uint32_t track, sa, sb;
 };
 
 struct ServeOut {
-  uint32_t count, seen, sep, pad;
+  uint32_t count, seen, sep, ndup, err, pad[3];
 };
 
 struct ServeTile {
@@ -64,18 +75,37 @@ struct ServeTile {
 struct StepArgs {
   const ServeSeg *segs;
   uint32_t nsegs;
-  const ServeTile *tiles;
+  ServeTile *tiles;              // listed by the kernel from each request's tile0 and ntiles
   uint32_t ntiles;
+  uint32_t *tile_cnt;            // per tile: states listed by the filter
   ServeOut *outs;
-  uint32_t max_stages;
+  uint32_t max_stages, any_filter;
+  uint32_t *seen1, *seen2, *seen3, *seen4;   // filter counters shared by the step's requests
+  uint32_t mbits;
   Ctrl *ctrl;
   unsigned long long barrier_ns;
 };
 
+// Tiles are dealt per block (block b: tiles b, b + grid, ... in order, its
+// warps taking the next from a shared counter reset after each barrier).
+__device__ __forceinline__ uint32_t serve_next_tile(const StepArgs &A, uint32_t *s_next) {
+  uint32_t i = 0;
+  if ((threadIdx.x & 31u) == 0) i = atomicAdd(s_next, 1u);
+  i = __shfl_sync(0xFFFFFFFFu, i, 0);
+  const uint64_t t = (uint64_t)blockIdx.x + (uint64_t)i * gridDim.x;
+  return t < A.ntiles ? (uint32_t)t : A.ntiles;
+}
+
+__device__ __forceinline__ void serve_start_tiles(uint32_t *s_next) {
+  if (threadIdx.x == 0) *s_next = 0u;
+  __syncthreads();
+}
+
+// Table round (stage `stage` of the request's plan) over one tile.
 template <bool ROUND1>
 __device__ __forceinline__ void serve_tile(const StepArgs &A, const ServeSeg &S, const ServeTile &T, uint32_t stage,
                                           bool last, CtaCache *cache) {
-  const StagePlan &P = ROUND1 ? S.plan1 : S.planr;
+  const StagePlan &P = S.plan;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t n = S.n, total = S.k + 1, bits = P.bits;
   uint32_t cbeg, cend;
@@ -141,30 +171,295 @@ __device__ __forceinline__ void serve_tile(const StepArgs &A, const ServeSeg &S,
   }
 }
 
+// Direct round over one tile: the packed signature is the new label, counted
+// through the request's bitmap (keys of at most 10 bits first in the warp's
+// shared bitmap).  The tile also clears its share of the other bitmap, which
+// the next round will use.
+static constexpr uint32_t kServeWarpBits = 10;
+template <bool ROUND1>
+__device__ __forceinline__ void serve_direct_tile(const StepArgs &A, const ServeSeg &S, const ServeTile &T, uint32_t t,
+                                                 uint32_t *wbm) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n = S.n, k = S.k, w = S.w;
+  const uint32_t *src = S.lab[(S.round - 1) & 1];
+  uint32_t *dst = S.lab[S.round & 1];
+  uint32_t *bm = S.bm[S.round & 1];
+  const unsigned long long keep = policy_evict_last();
+  const bool small = (k + 1) * w <= kServeWarpBits;
+  if (small) {
+    wbm[lane] = 0u;
+    __syncwarp();
+  }
+  uint32_t seen = 0, created = 0;
+  for (uint32_t base = 0; base < T.len; base += 32) {
+    const bool valid = base + lane < T.len;
+    const uint32_t q = T.start + (valid ? base + lane : 0u);
+    uint32_t key;
+    if (ROUND1) {
+      key = S.accept[q] != 0;
+      if (valid) seen |= key ? 1u : 2u;
+    } else {
+      key = src[q];
+    }
+    uint32_t shift = w;
+    for (uint32_t a = 0; a < k; ++a) {
+      const uint32_t d = S.delta[(size_t)a * n + q];   // validated at admission
+      const uint32_t c = ROUND1 ? (uint32_t)(S.accept[d] != 0) : ld_u32_hint(src + d, keep);
+      key |= c << shift;
+      shift += w;
+    }
+    if (valid) dst[q] = key;
+    const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, valid ? key : 0xFFFFFFFFu) & vm;
+    if (valid && lane == (uint32_t)(__ffs(grp) - 1)) {
+      const uint32_t bit = 1u << (key & 31u);
+      if (small) atomicOr(&wbm[key >> 5], bit);
+      else if (!(atomicOr(&bm[key >> 5], bit) & bit)) ++created;
+    }
+  }
+  if (small) {
+    __syncwarp();
+    const uint32_t v = wbm[lane];
+    if (v) created += __popc(v & ~atomicOr(&bm[lane], v));
+    __syncwarp();
+  }
+  // this tile's share of the next round's bitmap
+  const uint64_t words = ((1ull << S.log2S) + 31) / 32;
+  const uint64_t per = (words + S.ntiles - 1) / S.ntiles, lo = (uint64_t)(t - S.tile0) * per;
+  const uint64_t hi = lo + per < words ? lo + per : words;
+  uint32_t *nb = S.bm[(S.round + 1) & 1];
+  for (uint64_t i = lo + lane; i < hi; i += 32) nb[i] = 0u;
+  const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, created);
+  if (lane == 0 && wsum) atomicAdd(&A.outs[T.seg].count, wsum);
+  if (ROUND1) {
+    const uint32_t wseen = __reduce_or_sync(0xFFFFFFFFu, seen);
+    if (lane == 0 && wseen) atomicOr(&A.outs[T.seg].seen, wseen);
+  }
+}
+
+// Filter round, pass A over one tile: signature hash (the request's slot mixed
+// in) into the shared 2-bit counters; both buckets kept per state.
+__device__ __forceinline__ void serve_filter_a(const StepArgs &A, const ServeSeg &S, const ServeTile &T) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n = S.n, k = S.k;
+  const uint32_t *src = S.lab[(S.round - 1) & 1];
+  const unsigned long long keep = policy_evict_last();
+  for (uint32_t base = 0; base < T.len; base += 32) {
+    if (base + lane >= T.len) continue;
+    const uint32_t q = T.start + base + lane;
+    unsigned long long h = hash_step(0x243F6A8885A308D3ull ^ ((unsigned long long)T.seg * 0xD6E8FEB86659FD93ull),
+                                     src[q]);
+    for (uint32_t a = 0; a < k; ++a) h = hash_step(h, ld_u32_hint(src + S.delta[(size_t)a * n + q], keep));
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    const uint32_t b = (uint32_t)(h >> (64 - A.mbits));
+    const uint32_t bit = 1u << (b & 31u);
+    if (atomicOr(&A.seen1[b >> 5], bit) & bit) atomicOr(&A.seen2[b >> 5], bit);
+    S.tmp[q] = b;
+    unsigned long long h2 = (h ^ 0x9E3779B97F4A7C15ull) * 0xc4ceb9fe1a85ec53ull;
+    h2 ^= h2 >> 31;
+    S.tmp2[q] = (uint32_t)(h2 >> (64 - (A.mbits - 1)));
+  }
+}
+
+// Pass B over one tile: unique states keep their number as label; the others
+// are listed in the tile's own slice of the request's list and enter the
+// second filter.
+__device__ __forceinline__ void serve_filter_b(const StepArgs &A, const ServeSeg &S, const ServeTile &T, uint32_t t) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t *dst = S.lab[S.round & 1];
+  uint32_t *list = S.list + T.start, *list2 = S.list2 + T.start;
+  uint32_t cursor = 0, uniq = 0;
+  for (uint32_t base = 0; base < T.len; base += 32) {
+    const bool valid = base + lane < T.len;
+    const uint32_t q = T.start + base + lane;
+    bool dup = false;
+    uint32_t b2 = 0;
+    if (valid) {
+      const uint32_t b = S.tmp[q];
+      dup = (A.seen2[b >> 5] >> (b & 31u)) & 1u;
+      if (!dup) {
+        dst[q] = q;
+        ++uniq;
+      } else {
+        b2 = S.tmp2[q];
+        const uint32_t bit = 1u << (b2 & 31u);
+        if (atomicOr(&A.seen3[b2 >> 5], bit) & bit) atomicOr(&A.seen4[b2 >> 5], bit);
+      }
+    }
+    const unsigned dm = __ballot_sync(0xFFFFFFFFu, dup);
+    if (dup) {
+      const uint32_t p = cursor + __popc(dm & ((1u << lane) - 1u));
+      list[p] = q;
+      list2[p] = b2;
+    }
+    cursor += __popc(dm);
+  }
+  const uint32_t u = __reduce_add_sync(0xFFFFFFFFu, uniq);
+  if (lane == 0) {
+    A.tile_cnt[t] = cursor;
+    if (u) atomicAdd(&A.outs[T.seg].count, u);
+    if (cursor) atomicAdd(&A.outs[T.seg].ndup, cursor);
+  }
+}
+
+static constexpr uint32_t kServeResolved = 0x80000000u;   // listed state labelled by the second filter
+
+// Pass F over a tile's listed slice: a listed state alone in its second bucket
+// is unique too (marked resolved).
+__device__ __forceinline__ void serve_filter_f(const StepArgs &A, const ServeSeg &S, const ServeTile &T, uint32_t t) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t *dst = S.lab[S.round & 1];
+  uint32_t *list = S.list + T.start;
+  const uint32_t *list2 = S.list2 + T.start;
+  const uint32_t nd = A.tile_cnt[t];
+  uint32_t uniq = 0;
+  for (uint32_t i = lane; i < nd; i += 32) {
+    const uint32_t b2 = list2[i];
+    if (!((A.seen4[b2 >> 5] >> (b2 & 31u)) & 1u)) {
+      const uint32_t q = list[i];
+      dst[q] = q;
+      list[i] = q | kServeResolved;
+      ++uniq;
+    }
+  }
+  const uint32_t u = __reduce_add_sync(0xFFFFFFFFu, uniq);
+  if (lane == 0 && u) atomicAdd(&A.outs[T.seg].count, u);
+}
+
+// Pass D over a tile's listed slice: the states left insert their exact keys
+// (stage s of the plan tagged epoch0 + s) and each final slot keeps its
+// smallest member.
+__device__ __forceinline__ void serve_filter_d(const StepArgs &A, const ServeSeg &S, const ServeTile &T, uint32_t t) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t *list = S.list + T.start;
+  const uint32_t nd = A.tile_cnt[t];
+  const uint32_t *src = S.lab[(S.round - 1) & 1];
+  const unsigned long long keep = policy_evict_last();
+  const StagePlan &P = S.plan;
+  const uint32_t total = S.k + 1, mask = table_mask(S.log2S), w = S.w;
+  for (uint32_t i = lane; i < nd; i += 32) {
+    const uint32_t q = list[i];
+    if (q & kServeResolved) continue;
+    uint32_t slot[1] = {0u};
+    for (uint32_t st = 0; st < P.stages; ++st) {
+      u128 key[1] = {u128{0ull, 0ull}};
+      uint32_t shift = 0, cbeg, cend;
+      if (st == 0) {
+        cbeg = 0;
+        cend = P.first < total ? P.first : total;
+      } else {
+        put_bits(key[0], slot[0], 0);
+        shift = P.carry;
+        cbeg = P.first + (st - 1) * P.per;
+        cend = cbeg + P.per < total ? cbeg + P.per : total;
+      }
+      for (uint32_t j = cbeg; j < cend; ++j, shift += w)
+        put_bits(key[0], j == 0 ? src[q] : ld_u32_hint(src + S.delta[(size_t)(j - 1) * S.n + q], keep), shift);
+      const uint32_t ep = S.epoch0 + st;
+      key[0].hi |= (unsigned long long)ep << (64 - S.ebits);
+      slot[0] = (uint32_t)(mix128(key[0]) >> 32) & mask;
+      const bool want[1] = {true};
+      bool is_new[1];
+      table_insert_vec<1>(S.table, mask, key, S.ebits, ep, want, slot, is_new, &A.ctrl->err);
+    }
+    S.tmp[q] = slot[0];
+    atomicMax(&S.rep[slot[0]], ((unsigned long long)S.round << 32) | (unsigned long long)(~q));
+  }
+}
+
+// Pass C over a tile's listed slice: the states left take their slot's
+// smallest member as label; each slot's smallest member counts a block.
+__device__ __forceinline__ void serve_filter_c(const StepArgs &A, const ServeSeg &S, const ServeTile &T, uint32_t t) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t *dst = S.lab[S.round & 1];
+  const uint32_t *list = S.list + T.start;
+  const uint32_t nd = A.tile_cnt[t];
+  uint32_t first = 0;
+  for (uint32_t i = lane; i < nd; i += 32) {
+    const uint32_t q = list[i];
+    if (q & kServeResolved) continue;
+    const uint32_t m = ~(uint32_t)S.rep[S.tmp[q]];
+    dst[q] = m;
+    first += m == q;
+  }
+  const uint32_t u = __reduce_add_sync(0xFFFFFFFFu, first);
+  if (lane == 0 && u) atomicAdd(&A.outs[T.seg].count, u);
+}
+
 // One refinement round for every admitted request.
-__global__ void __launch_bounds__(kServeThreads) serve_step_kernel(StepArgs A) {
+__global__ void __launch_bounds__(kServeThreads, 2) serve_step_kernel(StepArgs A) {
   __shared__ CtaCache cache;
+  __shared__ uint32_t s_wbm[kServeThreads / 32][32];
+  __shared__ uint32_t s_next;
   Ctrl *C = A.ctrl;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  const uint32_t gwarp = tid >> 5, nwarps = stride >> 5;
+  const uint32_t lane = threadIdx.x & 31u, gwarp = tid >> 5, nwarps = stride >> 5;
   if (tid == 0) C->deadline = gtimer() + A.barrier_ns;
+  // tile list: request i's tiles are tile0 .. tile0 + ntiles - 1, one warp per request
+  for (uint32_t i = gwarp; i < A.nsegs; i += nwarps) {
+    const ServeSeg &S = A.segs[i];
+    for (uint32_t j = lane; j < S.ntiles; j += 32) {
+      const uint32_t start = j * kServeTile;
+      A.tiles[S.tile0 + j] = ServeTile{i, start, S.n - start < kServeTile ? S.n - start : kServeTile};
+    }
+  }
+  if (!grid_sync(C, A.barrier_ns)) return;
   for (uint32_t s = 0; s < A.max_stages; ++s) {
     cta_cache_clear(&cache);
-    for (uint32_t t = gwarp; t < A.ntiles; t += nwarps) {
+    serve_start_tiles(&s_next);
+    for (uint32_t t = serve_next_tile(A, &s_next); t < A.ntiles; t = serve_next_tile(A, &s_next)) {
       const ServeTile T = A.tiles[t];
       const ServeSeg &S = A.segs[T.seg];
+      if (ld_relaxed(S.err)) continue;   // invalid targets: never followed
       const bool round1 = S.round == 1;
-      const StagePlan &P = round1 ? S.plan1 : S.planr;
-      if (s >= P.stages) continue;
-      const bool last = s + 1 == P.stages;
-      if (round1) serve_tile<true>(A, S, T, s, last, &cache);
-      else serve_tile<false>(A, S, T, s, last, &cache);
+      if (S.mode == SM_DIRECT) {
+        if (s != 0) continue;
+        uint32_t *wbm = s_wbm[threadIdx.x >> 5];
+        if (round1) serve_direct_tile<true>(A, S, T, t, wbm);
+        else serve_direct_tile<false>(A, S, T, t, wbm);
+      } else if (S.mode == SM_FILTER) {
+        if (s == 0) serve_filter_a(A, S, T);
+      } else {
+        if (s >= S.plan.stages) continue;
+        const bool last = s + 1 == S.plan.stages;
+        if (round1) serve_tile<true>(A, S, T, s, last, &cache);
+        else serve_tile<false>(A, S, T, s, last, &cache);
+      }
     }
     if (!grid_sync(C, A.barrier_ns)) return;
+    if (s == 0 && A.any_filter) {
+      // filter passes B, F, D, C over the tiles of the requests in filter rounds
+      for (int pass = 0; pass < 4; ++pass) {
+        serve_start_tiles(&s_next);
+        for (uint32_t t = serve_next_tile(A, &s_next); t < A.ntiles; t = serve_next_tile(A, &s_next)) {
+          const ServeTile T = A.tiles[t];
+          const ServeSeg &S = A.segs[T.seg];
+          if (S.mode != SM_FILTER || ld_relaxed(S.err)) continue;
+          if (pass == 0) serve_filter_b(A, S, T, t);
+          else if (pass == 1) serve_filter_f(A, S, T, t);
+          else if (pass == 2) serve_filter_d(A, S, T, t);
+          else serve_filter_c(A, S, T, t);
+        }
+        if (pass == 3) {   // the counters start clean for the next filter step
+          for (uint64_t i = tid; i < ((uint64_t)1 << A.mbits) / 32; i += stride) {
+            A.seen1[i] = 0u;
+            A.seen2[i] = 0u;
+          }
+          for (uint64_t i = tid; i < ((uint64_t)1 << A.mbits) / 64; i += stride) {
+            A.seen3[i] = 0u;
+            A.seen4[i] = 0u;
+          }
+        }
+        if (!grid_sync(C, A.barrier_ns)) return;
+      }
+    }
   }
   for (uint32_t i = tid; i < A.nsegs; i += stride) {
     const ServeSeg &S = A.segs[i];
-    if (S.track) {
+    A.outs[i].err = ld_relaxed(S.err);
+    if (S.track && !A.outs[i].err) {
       const uint32_t *dst = S.lab[S.round & 1];
       A.outs[i].sep = dst[S.sa] != dst[S.sb];
     }
@@ -238,15 +533,18 @@ struct Req {
   std::vector<uint8_t> aA, aB;
   // placement
   size_t off = 0, bytes = 0;
-  size_t o_delta = 0, o_acc = 0, o_lab0 = 0, o_lab1 = 0, o_tmp = SIZE_MAX, o_table = 0, o_minrep = 0, o_flag = 0,
-         o_out = 0, o_err = 0;
-  uint32_t log2S = 0, ebits = 32;
-  StagePlan p1{}, pr{};
+  bool early = false;             // arena space taken and inputs copied in at submit
+  size_t o_delta = 0, o_acc = 0, o_lab0 = 0, o_lab1 = 0, o_tmp = 0, o_tmp2 = 0, o_list = 0, o_list2 = 0, o_table = 0,
+         o_rep = 0, o_bm0 = 0, o_bm1 = 0, o_minrep = 0, o_flag = 0, o_out = 0, o_err = 0;
+  uint32_t log2S = 0, wid = 1, ebits = 32;
   // progress
   uint32_t round = 0, changed = 0, prevB = 0, epoch = 0, lastB = 0, sep_round = 0xFFFFFFFFu;
+  uint32_t w = 1;                 // bits of the current labels
+  uint32_t mode = SM_TABLE;       // mode of the round in flight (or the last one)
+  bool fok = true;                // filter rounds allowed
   bool finished = false, converged = false;
   int status = DFA_OK;
-  std::vector<ServeTile> tiles;
+  uint32_t ntiles = 0;            // tiles of kServeTile states
   std::chrono::steady_clock::time_point t_submit, t_done;
   std::vector<uint32_t> blocks;
   dfa_result res{};
@@ -262,20 +560,66 @@ static size_t req_layout(Req &r) {
   };
   const uint64_t n = r.n;
   r.log2S = ceil_log2(n * 2 < 64 ? 64 : n * 2);
-  r.p1 = make_plan(r.k, 1, r.log2S);
-  r.pr = make_plan(r.k, r.log2S, r.log2S);
-  r.ebits = std::min(r.p1.ebits, r.pr.ebits);
+  r.wid = ceil_log2(n) > 0 ? ceil_log2(n) : 1;
+  // the epoch bits left free by every table or filter plan the request can take
+  // (label widths: 1 bit, (k+1)^j while direct, then log2S or wid bits)
+  r.ebits = 32;
+  if (r.k > 0) {
+    uint64_t w = 1;
+    while ((uint64_t)(r.k + 1) * w <= r.log2S) w *= r.k + 1;
+    for (const uint64_t x : {w, (uint64_t)r.log2S, (uint64_t)r.wid})
+      r.ebits = std::min(r.ebits, make_plan(r.k, (uint32_t)x, r.log2S).ebits);
+  }
+  const size_t S = (size_t)1 << r.log2S;
   r.o_err = take(4);
   r.o_delta = take((size_t)r.k * n * 4);
   r.o_acc = take(n);
   r.o_lab0 = take(n * 4);
   r.o_lab1 = take(n * 4);
-  r.o_tmp = (r.p1.stages > 1 || r.pr.stages > 1) ? take(n * 4) : SIZE_MAX;
-  r.o_table = take(((size_t)1 << r.log2S) * 16);
+  r.o_tmp = take(n * 4);
+  r.o_tmp2 = take(n * 4);
+  r.o_list = take(n * 4);
+  r.o_list2 = take(n * 4);
+  r.o_table = take(S * 16);
+  r.o_rep = take(S * 8);
+  r.o_bm0 = take(S / 8);
+  r.o_bm1 = take(S / 8);
   r.o_minrep = take(((size_t)1 << r.log2S) * 4);
   r.o_flag = take(n);
   r.o_out = take(n * 4);
   return off;
+}
+
+// Serving scratch (allocated once): control block, scan partials, per-slot
+// outputs and step descriptors, the step's tile list and per-tile listed
+// counts, and the filter counters (2^kServeMaxMbits buckets at most).
+static constexpr uint32_t kServeMaxMbits = 28;
+struct ServeScratch {
+  size_t ctrl, partials, outs, segs, tiles, tile_cnt, seen1, seen2, seen3, seen4, total;
+  size_t max_tiles;
+};
+
+static ServeScratch serve_scratch_layout(uint32_t max_slots, size_t max_tiles) {
+  ServeScratch L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  L.max_tiles = max_tiles;
+  L.ctrl = take(sizeof(Ctrl));
+  L.partials = take(kServeMaxGrid * 4);
+  L.outs = take((size_t)max_slots * sizeof(ServeOut));
+  L.segs = take((size_t)max_slots * sizeof(ServeSeg));
+  L.tiles = take(max_tiles * sizeof(ServeTile));
+  L.tile_cnt = take(max_tiles * 4);
+  L.seen1 = take(((size_t)1 << kServeMaxMbits) / 8);
+  L.seen2 = take(((size_t)1 << kServeMaxMbits) / 8);
+  L.seen3 = take(((size_t)1 << kServeMaxMbits) / 16);
+  L.seen4 = take(((size_t)1 << kServeMaxMbits) / 16);
+  L.total = off;
+  return L;
 }
 
 }  // namespace dfa
@@ -289,9 +633,12 @@ struct dfa_server {
   char *arena_base = nullptr;
   std::unique_ptr<Arena> arena;
   cudaStream_t stream = nullptr;
+  cudaStream_t in_stream = nullptr;   // submissions' copies into the arena
   // device scratch for steps and canonical numbering (allocated once)
   char *scratch = nullptr;
-  size_t scratch_bytes = 0;
+  ServeScratch sl{};
+  ServeSeg *segs_pinned = nullptr;
+  ServeOut *outs_pinned = nullptr;
   int grid_step = 0, grid_canon = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -310,12 +657,6 @@ struct dfa_server {
 namespace dfa {
 
 static constexpr uint32_t kServeMaxSlots = 4096;
-
-// scratch: Ctrl (256) | partials (kServeMaxGrid*4) | outs (max_slots*16) | segs | tiles staging
-static size_t serve_scratch_size(uint32_t max_slots, size_t max_tiles) {
-  return 256 + kServeMaxGrid * 4 + (size_t)max_slots * sizeof(ServeOut) + (size_t)max_slots * sizeof(ServeSeg) +
-         max_tiles * sizeof(ServeTile) + 4096;
-}
 
 static void finish_req(dfa_server *s, const std::shared_ptr<Req> &r, int status) {
   r->status = status;
@@ -343,14 +684,17 @@ static cudaError_t place_req(dfa_server *s, Req &r) {
   cudaStream_t st = s->stream;
   cudaError_t e = cudaMemsetAsync(b + r.o_err, 0, 4, st);
   const uint32_t n = r.n;
-  if (e == cudaSuccess && r.k > 0)
-    e = cudaMemcpy2DAsync(b + r.o_delta, (size_t)n * 4, r.dA.data(), (size_t)r.nA * 4, (size_t)r.nA * 4, r.k,
-                          cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && r.k > 0 && r.nB > 0)
-    e = cudaMemcpy2DAsync(b + r.o_delta + (size_t)r.nA * 4, (size_t)n * 4, r.dB.data(), (size_t)r.nB * 4,
-                          (size_t)r.nB * 4, r.k, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b + r.o_acc, r.aA.data(), r.nA, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && r.nB > 0) e = cudaMemcpyAsync(b + r.o_acc + r.nA, r.aB.data(), r.nB, cudaMemcpyHostToDevice, st);
+  if (!r.early) {   // inputs held on the host since submit
+    if (e == cudaSuccess && r.k > 0)
+      e = cudaMemcpy2DAsync(b + r.o_delta, (size_t)n * 4, r.dA.data(), (size_t)r.nA * 4, (size_t)r.nA * 4, r.k,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && r.k > 0 && r.nB > 0)
+      e = cudaMemcpy2DAsync(b + r.o_delta + (size_t)r.nA * 4, (size_t)n * 4, r.dB.data(), (size_t)r.nB * 4,
+                            (size_t)r.nB * 4, r.k, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + r.o_acc, r.aA.data(), r.nA, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && r.nB > 0)
+      e = cudaMemcpyAsync(b + r.o_acc + r.nA, r.aB.data(), r.nB, cudaMemcpyHostToDevice, st);
+  }
   if (e != cudaSuccess) return e;
   uint32_t *du = reinterpret_cast<uint32_t *>(b + r.o_delta);
   uint32_t *err = reinterpret_cast<uint32_t *>(b + r.o_err);
@@ -361,27 +705,32 @@ static cudaError_t place_req(dfa_server *s, Req &r) {
       if (e != cudaSuccess) return e;
     }
   }
-  e = cudaMemsetAsync(b + r.o_table, 0, ((size_t)1 << r.log2S) * 16, st);
+  const size_t S = (size_t)1 << r.log2S;
+  e = cudaMemsetAsync(b + r.o_table, 0, S * 16, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b + r.o_rep, 0, S * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b + r.o_bm0, 0, S / 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b + r.o_bm1, 0, S / 8, st);
   if (e != cudaSuccess) return e;
-  r.tiles.clear();
-  for (uint32_t t = 0; t * kServeTile < n; ++t) r.tiles.push_back(ServeTile{0, t * kServeTile, std::min(kServeTile, n - t * kServeTile)});
+  r.ntiles = (n + kServeTile - 1) / kServeTile;
   r.round = 0;
   r.epoch = 0;
+  r.w = 1;
+  r.fok = true;
   return cudaGetLastError();
 }
 
 static void worker_main(dfa_server *s) {
   cudaSetDevice(s->device);
   char *sc = s->scratch;
-  Ctrl *ctrl = reinterpret_cast<Ctrl *>(sc);
-  uint32_t *partials = reinterpret_cast<uint32_t *>(sc + 256);
-  ServeOut *outs = reinterpret_cast<ServeOut *>(sc + 256 + kServeMaxGrid * 4);
-  ServeSeg *segs_d = reinterpret_cast<ServeSeg *>(reinterpret_cast<char *>(outs) + (size_t)s->max_slots * sizeof(ServeOut));
-  ServeTile *tiles_d = reinterpret_cast<ServeTile *>(reinterpret_cast<char *>(segs_d) + (size_t)s->max_slots * sizeof(ServeSeg));
-  const size_t max_tiles = (s->scratch_bytes - (reinterpret_cast<char *>(tiles_d) - sc)) / sizeof(ServeTile);
-  std::vector<ServeSeg> segs_h;
-  std::vector<ServeTile> tiles_h;
-  std::vector<ServeOut> outs_h;
+  Ctrl *ctrl = reinterpret_cast<Ctrl *>(sc + s->sl.ctrl);
+  uint32_t *partials = reinterpret_cast<uint32_t *>(sc + s->sl.partials);
+  ServeOut *outs = reinterpret_cast<ServeOut *>(sc + s->sl.outs);
+  ServeSeg *segs_d = reinterpret_cast<ServeSeg *>(sc + s->sl.segs);
+  ServeTile *tiles_d = reinterpret_cast<ServeTile *>(sc + s->sl.tiles);
+  uint32_t *tile_cnt = reinterpret_cast<uint32_t *>(sc + s->sl.tile_cnt);
+  const size_t max_tiles = s->sl.max_tiles;
+  ServeSeg *segs_h = s->segs_pinned;   // pinned: the step's copies are truly asynchronous
+  ServeOut *outs_h = s->outs_pinned;
   while (true) {
     std::vector<std::shared_ptr<Req>> admitted;
     {
@@ -391,14 +740,16 @@ static void worker_main(dfa_server *s) {
       if (s->stop) break;
       // admission in arrival order while a slot and arena space are free
       size_t tiles_now = 0;
-      for (auto &r : s->active) tiles_now += r->tiles.size();
+      for (auto &r : s->active) tiles_now += r->ntiles;
       while (!s->queue.empty() && s->active.size() < s->max_slots) {
         auto r = s->queue.front();
         const size_t want_tiles = (r->n + kServeTile - 1) / kServeTile;
         if (tiles_now + want_tiles > max_tiles) break;
-        size_t off;
-        if (!s->arena->alloc(r->bytes, &off)) break;
-        r->off = off;
+        if (!r->early) {
+          size_t off;
+          if (!s->arena->alloc(r->bytes, &off)) break;
+          r->off = off;
+        }
         s->queue.pop_front();
         s->active.push_back(r);
         admitted.push_back(r);
@@ -413,17 +764,8 @@ static void worker_main(dfa_server *s) {
         finish_req(s, r, DFA_ECUDA);
       }
     }
-    if (!admitted.empty()) {
-      // requests whose targets were out of range finish with DFA_EINVAL
-      std::vector<uint32_t> errs(admitted.size());
-      for (size_t i = 0; i < admitted.size(); ++i)
-        cudaMemcpyAsync(&errs[i], s->arena_base + admitted[i]->off + admitted[i]->o_err, 4, cudaMemcpyDeviceToHost,
-                        s->stream);
-      cudaStreamSynchronize(s->stream);
-      std::lock_guard<std::mutex> lock(s->mu);
-      for (size_t i = 0; i < admitted.size(); ++i)
-        if (errs[i] && !admitted[i]->finished) finish_req(s, admitted[i], DFA_EINVAL);
-    }
+    // (requests whose targets fail validation are skipped by the step kernel and
+    // finish with DFA_EINVAL when the step's outputs come back)
     std::vector<std::shared_ptr<Req>> act;
     {
       std::lock_guard<std::mutex> lock(s->mu);
@@ -434,15 +776,20 @@ static void worker_main(dfa_server *s) {
     }
     if (act.empty()) continue;
     // ---- one round for every admitted request
-    segs_h.clear();
-    tiles_h.clear();
-    uint32_t max_stages = 1;
+    uint32_t ntiles = 0;
+    uint32_t max_stages = 1, any_filter = 0;
+    uint64_t filter_states = 0;
     for (uint32_t i = 0; i < act.size(); ++i) {
       Req &r = *act[i];
       r.round += 1;
-      const StagePlan &P = r.round == 1 ? r.p1 : r.pr;
+      // the round's mode, as dfa_minimise chooses it
+      if ((uint64_t)(r.k + 1) * r.w <= r.log2S) r.mode = SM_DIRECT;
+      else if (r.round > 1 && r.fok && (uint64_t)r.prevB * 64 >= r.n) r.mode = SM_FILTER;
+      else r.mode = SM_TABLE;
+      const StagePlan P = make_plan(r.k, r.w, r.log2S);
+      const uint32_t stages = r.mode == SM_DIRECT ? 0u : P.stages;
       const uint32_t emax = r.ebits >= 32 ? 0xFFFFFFFFu : ((1u << r.ebits) - 1u);
-      if ((uint64_t)r.epoch + P.stages > emax) {   // epochs would wrap: clear this request's table
+      if ((uint64_t)r.epoch + stages > emax) {   // epochs would wrap: clear this request's table
         cudaMemsetAsync(s->arena_base + r.off + r.o_table, 0, ((size_t)1 << r.log2S) * 16, s->stream);
         r.epoch = 0;
       }
@@ -454,44 +801,61 @@ static void worker_main(dfa_server *s) {
       g.k = r.k;
       g.lab[0] = reinterpret_cast<uint32_t *>(b + r.o_lab0);
       g.lab[1] = reinterpret_cast<uint32_t *>(b + r.o_lab1);
-      g.tmp = r.o_tmp == SIZE_MAX ? nullptr : reinterpret_cast<uint32_t *>(b + r.o_tmp);
+      g.tmp = reinterpret_cast<uint32_t *>(b + r.o_tmp);
+      g.tmp2 = reinterpret_cast<uint32_t *>(b + r.o_tmp2);
+      g.list = reinterpret_cast<uint32_t *>(b + r.o_list);
+      g.list2 = reinterpret_cast<uint32_t *>(b + r.o_list2);
       g.table = reinterpret_cast<u128 *>(b + r.o_table);
+      g.rep = reinterpret_cast<unsigned long long *>(b + r.o_rep);
+      g.bm[0] = reinterpret_cast<uint32_t *>(b + r.o_bm0);
+      g.bm[1] = reinterpret_cast<uint32_t *>(b + r.o_bm1);
       g.log2S = r.log2S;
+      g.wid = r.wid;
       g.ebits = r.ebits;
-      g.plan1 = r.p1;
-      g.planr = r.pr;
+      g.mode = r.mode;
+      g.w = r.w;
+      g.plan = P;
       g.round = r.round;
       g.epoch0 = r.epoch + 1;
+      g.tile0 = ntiles;
+      g.ntiles = r.ntiles;
+      g.err = reinterpret_cast<const uint32_t *>(b + r.o_err);
       g.track = r.kind == DFA_REQ_EQUIVALENT;
       g.sa = r.sA;
       g.sb = r.nA + r.sB;
-      r.epoch += P.stages;
-      max_stages = std::max(max_stages, P.stages);
-      segs_h.push_back(g);
-      for (ServeTile t : r.tiles) {
-        t.seg = i;
-        tiles_h.push_back(t);
+      r.epoch += stages;
+      if (r.mode == SM_TABLE) max_stages = std::max(max_stages, P.stages);
+      if (r.mode == SM_FILTER) {
+        any_filter = 1;
+        filter_states += r.n;
       }
+      segs_h[i] = g;
+      ntiles += r.ntiles;
     }
-    cudaMemcpyAsync(segs_d, segs_h.data(), segs_h.size() * sizeof(ServeSeg), cudaMemcpyHostToDevice, s->stream);
-    cudaMemcpyAsync(tiles_d, tiles_h.data(), tiles_h.size() * sizeof(ServeTile), cudaMemcpyHostToDevice, s->stream);
+    cudaMemcpyAsync(segs_d, segs_h, act.size() * sizeof(ServeSeg), cudaMemcpyHostToDevice, s->stream);
     cudaMemsetAsync(outs, 0, act.size() * sizeof(ServeOut), s->stream);
     cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s->stream);
     StepArgs a{};
     a.segs = segs_d;
     a.nsegs = (uint32_t)act.size();
     a.tiles = tiles_d;
-    a.ntiles = (uint32_t)tiles_h.size();
+    a.ntiles = ntiles;
     a.outs = outs;
+    a.tile_cnt = tile_cnt;
     a.max_stages = max_stages;
+    a.any_filter = any_filter;
+    a.seen1 = reinterpret_cast<uint32_t *>(sc + s->sl.seen1);
+    a.seen2 = reinterpret_cast<uint32_t *>(sc + s->sl.seen2);
+    a.seen3 = reinterpret_cast<uint32_t *>(sc + s->sl.seen3);
+    a.seen4 = reinterpret_cast<uint32_t *>(sc + s->sl.seen4);
+    a.mbits = std::min<uint32_t>(kServeMaxMbits, std::max<uint32_t>(12, ceil_log2(filter_states + 1) + 2));
     a.ctrl = ctrl;
     a.barrier_ns = 5000000000ull;
     void *params[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)serve_step_kernel, dim3(s->grid_step),
                                                 dim3(kServeThreads), params, 0, s->stream);
-    outs_h.resize(act.size());
     Ctrl ch{};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(outs_h.data(), outs, act.size() * sizeof(ServeOut), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(outs_h, outs, act.size() * sizeof(ServeOut), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ch, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess || ch.err) {
@@ -507,9 +871,18 @@ static void worker_main(dfa_server *s) {
     for (uint32_t i = 0; i < act.size(); ++i) {
       Req &r = *act[i];
       const ServeOut &o = outs_h[i];
+      if (o.err) {   // targets out of range: the request never ran
+        r.status = DFA_EINVAL;
+        done.push_back(act[i]);
+        continue;
+      }
       const uint32_t prev = r.round == 1 ? (uint32_t)__builtin_popcount(o.seen) : r.prevB;
       const uint32_t B = o.count;
       r.lastB = B;
+      // width of this round's labels; a filter round that listed most states
+      // (large blocks) hands later rounds to the table
+      r.w = r.mode == SM_DIRECT ? (r.k + 1) * r.w : r.mode == SM_FILTER ? r.wid : r.log2S;
+      if (r.mode == SM_FILTER && (uint64_t)o.ndup * 2 > r.n) r.fok = false;
       const bool grew = B != prev;
       if (grew) r.changed += 1;
       bool fin = false;
@@ -535,12 +908,12 @@ static void worker_main(dfa_server *s) {
     }
     for (auto &rp : done) {
       Req &r = *rp;
-      if (r.kind == DFA_REQ_MINIMISE) {
+      if (r.kind == DFA_REQ_MINIMISE && (r.status == DFA_OK || r.status == DFA_EMAXROUNDS)) {   // labels valid
         char *b = s->arena_base + r.off;
         CanonArgs ca{r.n, reinterpret_cast<uint32_t *>(b + (r.round & 1 ? r.o_lab1 : r.o_lab0)),
                      (size_t)1 << r.log2S, reinterpret_cast<uint32_t *>(b + r.o_minrep),
                      reinterpret_cast<uint8_t *>(b + r.o_flag), partials, reinterpret_cast<uint32_t *>(b + r.o_out),
-                     ctrl, 5000000000ull, 0u};
+                     ctrl, 5000000000ull, r.mode == SM_FILTER ? 1u : 0u};   // filter labels: smallest members
         uint32_t B = r.lastB;
         cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s->stream);
         void *cp[] = {&ca, &B};
@@ -561,6 +934,30 @@ static void worker_main(dfa_server *s) {
       if (!done.empty()) s->cv_done.notify_all();
     }
   }
+}
+
+// Copies a request's inputs straight into its arena region (A's columns
+// first, then B's; B's targets are offset on the device at admission) on the
+// server's input stream, and waits for the copies so the caller may free them.
+static int copy_in_device(dfa_server *s, Req &r, const dfa_t *a, const dfa_t *b) {
+  char *base = s->arena_base + r.off;
+  cudaStream_t st = s->in_stream;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaError_t e = cudaSetDevice(s->device);
+  if (r.k > 0)
+    e = cudaMemcpy2DAsync(base + r.o_delta, (size_t)r.n * 4, a->delta, (size_t)r.nA * 4, (size_t)r.nA * 4, r.k,
+                          cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(base + r.o_acc, a->accept, r.nA, cudaMemcpyDefault, st);
+  if (b) {
+    if (e == cudaSuccess && r.k > 0)
+      e = cudaMemcpy2DAsync(base + r.o_delta + (size_t)r.nA * 4, (size_t)r.n * 4, b->delta, (size_t)r.nB * 4,
+                            (size_t)r.nB * 4, r.k, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + r.o_acc + r.nA, b->accept, r.nB, cudaMemcpyDefault, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaSetDevice(prev);
+  return e == cudaSuccess ? DFA_OK : cuda_fail(e, "copy request in");
 }
 
 static int copy_dfa_in(const dfa_t *d, std::vector<uint32_t> &delta, std::vector<uint8_t> &acc) {
@@ -590,17 +987,24 @@ int dfa_serve_create(dfa_server **out, size_t hbm_budget_bytes, uint32_t max_slo
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   const size_t max_tiles = hbm_budget_bytes / (kServeTile * 16) + max_slots + 1024;
-  s->scratch_bytes = serve_scratch_size(max_slots, max_tiles);
+  s->sl = serve_scratch_layout(max_slots, max_tiles);
   e = cudaMalloc(&s->arena_base, hbm_budget_bytes);
   if (e != cudaSuccess) return fail(DFA_ENOMEM, "cannot allocate the %zu-byte arena: %s", hbm_budget_bytes,
                                     cudaGetErrorString(e));
-  e = cudaMalloc(&s->scratch, s->scratch_bytes);
+  e = cudaMalloc(&s->scratch, s->sl.total);
   if (e != cudaSuccess) {
     cudaFree(s->arena_base);
     return fail(DFA_ENOMEM, "cannot allocate serving scratch: %s", cudaGetErrorString(e));
   }
+  e = cudaMallocHost(&s->segs_pinned, (size_t)max_slots * sizeof(ServeSeg));
+  if (e == cudaSuccess) e = cudaMallocHost(&s->outs_pinned, (size_t)max_slots * sizeof(ServeOut));
+  if (e != cudaSuccess) return fail(DFA_ENOMEM, "cannot allocate pinned step buffers: %s", cudaGetErrorString(e));
+  // the filter counters start clean (each filter step clears what it used)
+  e = cudaMemset(s->scratch + s->sl.seen1, 0, s->sl.total - s->sl.seen1);
+  if (e != cudaSuccess) return cuda_fail(e, "clear serving scratch");
   s->arena = std::make_unique<Arena>(hbm_budget_bytes);
   e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->in_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -638,11 +1042,42 @@ int dfa_serve_submit(dfa_server *s, int kind, const dfa_t *a, const dfa_t *b, co
   r->n = r->nA + r->nB;
   r->bytes = req_layout(*r);
   if (r->bytes > s->budget) return fail(DFA_ENOMEM, "request needs %zu bytes, budget is %zu", r->bytes, s->budget);
-  rc = copy_dfa_in(a, r->dA, r->aA);
-  if (rc != DFA_OK) return rc;
+  // round 0 of an equivalence request: the empty word already separates start
+  // states of different acceptance; with early exit no round is needed
+  uint8_t acc_a = 0, acc_b = 0;
   if (kind == DFA_REQ_EQUIVALENT) {
-    rc = copy_dfa_in(b, r->dB, r->aB);
-    if (rc != DFA_OK) return rc;
+    cudaError_t e = cudaMemcpy(&acc_a, a->accept + a->start, 1, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemcpy(&acc_b, b->accept + b->start, 1, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "read start acceptance");
+  }
+  const bool sep0 = kind == DFA_REQ_EQUIVALENT && ((acc_a != 0) != (acc_b != 0));
+  const bool instant = sep0 && (r->o.flags & DFA_FLAG_EARLY_EXIT);
+  if (!instant) {
+    // inputs go straight into the request's arena region when it has room now;
+    // otherwise they wait on the host until admission
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      size_t off;
+      if (s->arena->alloc(r->bytes, &off)) {
+        r->off = off;
+        r->early = true;
+      }
+    }
+    if (r->early) {
+      rc = copy_in_device(s, *r, a, kind == DFA_REQ_EQUIVALENT ? b : nullptr);
+      if (rc != DFA_OK) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->arena->release(r->off, r->bytes);
+        return rc;
+      }
+    } else {
+      rc = copy_dfa_in(a, r->dA, r->aA);
+      if (rc != DFA_OK) return rc;
+      if (kind == DFA_REQ_EQUIVALENT) {
+        rc = copy_dfa_in(b, r->dB, r->aB);
+        if (rc != DFA_OK) return rc;
+      }
+    }
   }
   r->t_submit = std::chrono::steady_clock::now();
   {
@@ -653,11 +1088,8 @@ int dfa_serve_submit(dfa_server *s, int kind, const dfa_t *a, const dfa_t *b, co
       s->any_submit = true;
     }
     s->all[r->ticket] = r;
-    // round 0 of an equivalence request: the empty word already separates start
-    // states of different acceptance; with early exit no round is needed
-    const bool sep0 = kind == DFA_REQ_EQUIVALENT && ((r->aA[r->sA] != 0) != (r->aB[r->sB] != 0));
     if (sep0) r->sep_round = 0;
-    if (sep0 && (r->o.flags & DFA_FLAG_EARLY_EXIT)) {
+    if (instant) {
       r->finished = true;
       r->status = DFA_OK;
       r->equivalent = 0;
@@ -755,8 +1187,11 @@ int dfa_serve_destroy(dfa_server *s) {
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->in_stream) cudaStreamDestroy(s->in_stream);
   if (s->arena_base) cudaFree(s->arena_base);
   if (s->scratch) cudaFree(s->scratch);
+  if (s->segs_pinned) cudaFreeHost(s->segs_pinned);
+  if (s->outs_pinned) cudaFreeHost(s->outs_pinned);
   delete s;
   return DFA_OK;
 }
