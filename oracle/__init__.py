@@ -297,6 +297,17 @@ def trans_pr(delta, accept, max_rounds: int | None = None) -> RefineResult:
     return naive_pr(closure(delta), accept, max_rounds=max_rounds)
 
 
+def closure_moore(delta, accept, max_rounds: int | None = None, history: bool = False,
+                  stop_discrete: bool = False) -> RefineResult:
+    """Signature refinement (Algorithm 4) on the extended DFA A' of Algorithm 5
+    (letters a^(2^i), i = 0..floor(log2 n)) instead of naivePR.  The extra letters
+    are words over Σ and Σ's own letters are level 0 of δT, so A' and A have the
+    same coarsest congruence (the Nerode partition); a round of A' tests words
+    of up to 2^L letters of A at once."""
+    delta, accept = _prep(delta, accept)
+    return moore(closure(delta), accept, max_rounds=max_rounds, history=history, stop_discrete=stop_discrete)
+
+
 # ----------------------------------------------------------------------------
 # Equivalence (Section 4): refine the disjoint union
 # ----------------------------------------------------------------------------

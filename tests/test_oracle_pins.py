@@ -343,3 +343,49 @@ def test_pins_catch_broken_closure():
     for _ in range(4):
         cur = A.delta[0][cur]
     assert np.array_equal(T[2], cur) and not np.array_equal(broken[2], cur)
+
+
+# ---------------------------------------------------------------- closure + signature refinement
+
+def _closure_moore_cases():
+    yield dfagen.random_dfa(500, 2, 0.5, 11)
+    yield dfagen.random_dfa(300, 3, 0.3, 12)
+    yield dfagen.random_dfa(200, 0, 0.5, 13)
+    yield dfagen.fibonacci_dfa(10)
+    yield dfagen.bit_splitter(5)
+    yield dfagen.chain_dfa(100)
+    yield dfagen.cycle_dfa(9)
+    yield dfagen.fig1_chain()
+    yield dfagen.planted_redundancy(dfagen.random_dfa(120, 3, 0.5, 14), 4, 3)[0]
+
+
+@pytest.mark.parametrize("idx", range(9))
+def test_closure_moore_partition_is_nerode(idx):
+    """The closure letters are words over Σ, so refining A' gives A's coarsest
+    congruence: the same partition as Hopcroft and as plain refinement."""
+    A = list(_closure_moore_cases())[idx]
+    r = oracle.closure_moore(A.delta, A.accept)
+    assert np.array_equal(r.block, oracle.hopcroft(A.delta, A.accept))
+    assert np.array_equal(r.block, oracle.moore(A.delta, A.accept).block)
+    assert r.rounds_executed <= oracle.moore(A.delta, A.accept).rounds_executed
+
+
+@pytest.mark.parametrize("n", [3, 5, 10, 64, 100, 256, 1000])
+def test_closure_moore_chain_closed_form(n):
+    """Chain: state q is at distance d = n-1-q from the accepting state; only
+    powers a^s separate states (b resets to state 0), and a^s accepts from
+    distance d iff s >= d.  r closure letters spell a^s iff popcount(s) <= r,
+    so distances d and d-1 first differ in round popcount(d-1): the refinement
+    grows in every round up to max popcount(x), 1 <= x <= n-2."""
+    C = dfagen.chain_dfa(n)
+    r = oracle.closure_moore(C.delta, C.accept)
+    R = max(bin(x).count("1") for x in range(1, n - 1))
+    assert r.num_blocks == n
+    assert (r.rounds_changed, r.rounds_executed) == (R, R + 1)
+
+
+def test_closure_moore_fig1_first_round():
+    """Section 3.4's example: with the closure, q0 and q1 part in the first round."""
+    C = dfagen.fig1_chain()
+    r = oracle.closure_moore(C.delta, C.accept, history=True)
+    assert r.history[1][0] != r.history[1][1]
