@@ -71,7 +71,12 @@ typedef enum dfa_status {
 typedef enum dfa_algo {
   DFA_ALGO_MOORE = 0,     /* signature refinement, Section 3.3 / Algorithm 4 (sortPR's result) */
   DFA_ALGO_NAIVE = 1,     /* leader-election refinement, Section 3.2 / Algorithm 2 */
-  DFA_ALGO_TRANS = 2      /* partial transitive closure + naivePR, Section 3.4 / Algorithm 5 */
+  DFA_ALGO_TRANS = 2,     /* partial transitive closure + naivePR, Section 3.4 / Algorithm 5 */
+  DFA_ALGO_CLOSURE_MOORE = 3  /* Algorithm 5's closure table feeding signature refinement (Algorithm 4)
+                                 instead of naivePR: same partition (the extra letters are words over
+                                 the alphabet); rounds are those of Algorithm 4 on the extended DFA,
+                                 on the n-state chain max popcount(x), 1 <= x <= n - 2, of them.  An
+                                 extension the paper leaves open (it asks for sublinear refinement). */
 } dfa_algo;
 
 /* Flags for dfa_opts.flags */

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libdfa_gb300.so")
 DFA_OK, DFA_EINVAL, DFA_ENOMEM, DFA_ECUDA, DFA_ETIMEOUT, DFA_EMAXROUNDS, DFA_EBUSY, DFA_ECANCELLED = 0, -1, -2, -3, -4, -5, -6, -7
 STATUS_NAMES = {0: "DFA_OK", -1: "DFA_EINVAL", -2: "DFA_ENOMEM", -3: "DFA_ECUDA", -4: "DFA_ETIMEOUT",
                 -5: "DFA_EMAXROUNDS", -6: "DFA_EBUSY", -7: "DFA_ECANCELLED"}
-ALGOS = {"moore": 0, "naive": 1, "trans": 2}
+ALGOS = {"moore": 0, "naive": 1, "trans": 2, "closure_moore": 3}
 DFA_FLAG_EARLY_EXIT = 0x1
 DFA_FLAG_TABLE_ONLY = 0x2
 DFA_FLAG_STOP_DISCRETE = 0x4

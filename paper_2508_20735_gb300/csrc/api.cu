@@ -217,6 +217,80 @@ uint32_t pick_vec(uint32_t n, uint32_t k, const void *delta, const void *accept,
 
 }  // namespace dfa
 
+namespace dfa {
+
+// Signature refinement on the closure DFA: [closure table | Moore workspace for
+// (n, k (L+1)) letters | staged δ when the caller passes host memory].
+struct ClosureMooreLayout {
+  uint32_t L;
+  size_t dT, moore, delta, total;
+  MooreLayout m;
+};
+
+static ClosureMooreLayout closure_moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_accept) {
+  ClosureMooreLayout C{};
+  C.L = (uint32_t)(63 - __builtin_clzll((unsigned long long)n));
+  const size_t rows = (size_t)k * (C.L + 1);
+  C.dT = 0;
+  C.moore = (rows * n * 4 + 255) / 256 * 256;
+  C.m = moore_layout(n, (uint32_t)rows, false, stage_accept, true);
+  C.delta = C.moore + (C.m.total + 255) / 256 * 256;
+  C.total = C.delta + (stage_delta ? ((size_t)k * n * 4 + 255) / 256 * 256 : 0);
+  return C;
+}
+
+static int run_closure_moore(const dfa_t *d, const dfa_opts &o, uint32_t *block_out, dfa_result *res,
+                             void *workspace, size_t ws_bytes, cudaStream_t st) {
+  const bool hd = d->k > 0 && !is_device_ptr(d->delta);
+  const bool ha = !is_device_ptr(d->accept);
+  const bool ho = !is_device_ptr(block_out);
+  const ClosureMooreLayout C = closure_moore_layout(d->n, d->k, hd, ha);
+  if (ws_bytes < C.total) return fail(DFA_EINVAL, "workspace too small: %zu < %zu bytes", ws_bytes, C.total);
+  char *ws = static_cast<char *>(workspace);
+  char *wm = ws + C.moore;
+  const uint32_t *delta = d->delta;
+  const uint8_t *accept = d->accept;
+  cudaError_t e;
+  if (hd) {
+    e = cudaMemcpyAsync(ws + C.delta, d->delta, (size_t)d->k * d->n * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy delta to device");
+    delta = reinterpret_cast<const uint32_t *>(ws + C.delta);
+  }
+  if (ha) {
+    e = cudaMemcpyAsync(wm + C.m.accept, d->accept, d->n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy accept to device");
+    accept = reinterpret_cast<const uint8_t *>(wm + C.m.accept);
+  }
+  uint32_t *dT = reinterpret_cast<uint32_t *>(ws + C.dT);
+  Ctrl cc{};
+  int rc = run_closure(delta, d->n, d->k, dT, reinterpret_cast<Ctrl *>(wm + C.m.ctrl), o, st, &cc);
+  if (rc != DFA_OK) return rc;
+  rc = status_from_ctrl(cc);
+  if (rc != DFA_OK) return rc;
+  const uint32_t rows = d->k * (C.L + 1);
+  uint32_t *out = ho ? reinterpret_cast<uint32_t *>(wm + C.m.out) : block_out;
+  Ctrl c{};
+  rc = run_moore(dT, accept, d->n, rows, out, C.m, wm, o, st, nullptr, &c, 1u);
+  if (rc != DFA_OK) return rc;
+  const int status = status_from_ctrl(c);
+  if (res) {
+    res->num_blocks = c.num_blocks;
+    res->rounds_changed = c.rounds_changed;
+    res->rounds_executed = c.rounds_executed;
+    res->status = status;
+    res->device_ns = (cc.t_end - cc.t_start) + (c.t_end - c.t_start);
+  }
+  if (status != DFA_OK && status != DFA_EMAXROUNDS) return status;
+  if (ho) {
+    e = cudaMemcpyAsync(block_out, out, (size_t)d->n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy blocks to host");
+  }
+  return status;
+}
+
+}  // namespace dfa
+
 using namespace dfa;
 
 extern "C" {
@@ -228,11 +302,10 @@ const char *dfa_version(void) { return "dfa_gb300 0.1 (sm_103a)"; }
 size_t dfa_workspace_size(const dfa_t *d, const dfa_opts *opts) {
   if (check_dfa(d, "dfa") != DFA_OK) return 0;
   const dfa_opts o = default_opts(opts);
-  if (o.algo == DFA_ALGO_MOORE) {
-    const bool hd = d->k > 0 && !is_device_ptr(d->delta);
-    const bool ha = !is_device_ptr(d->accept);
-    return moore_layout(d->n, d->k, hd, ha, true).total;
-  }
+  const bool hd = d->k > 0 && !is_device_ptr(d->delta);
+  const bool ha = !is_device_ptr(d->accept);
+  if (o.algo == DFA_ALGO_MOORE) return moore_layout(d->n, d->k, hd, ha, true).total;
+  if (o.algo == DFA_ALGO_CLOSURE_MOORE) return closure_moore_layout(d->n, d->k, hd, ha).total;
   return naive_workspace_size(d, o);
 }
 
@@ -244,9 +317,11 @@ int dfa_minimise(const dfa_t *d, const dfa_opts *opts, uint32_t *block_out, dfa_
   if (!workspace) return fail(DFA_EINVAL, "workspace is NULL");
   if (!aligned(workspace, 256)) return fail(DFA_EINVAL, "workspace must be 256-byte aligned");
   const dfa_opts o = default_opts(opts);
-  if (o.algo != DFA_ALGO_MOORE && o.algo != DFA_ALGO_NAIVE && o.algo != DFA_ALGO_TRANS)
+  if (o.algo != DFA_ALGO_MOORE && o.algo != DFA_ALGO_NAIVE && o.algo != DFA_ALGO_TRANS &&
+      o.algo != DFA_ALGO_CLOSURE_MOORE)
     return fail(DFA_EINVAL, "unknown algo %d", o.algo);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (o.algo == DFA_ALGO_CLOSURE_MOORE) return run_closure_moore(d, o, block_out, res, workspace, ws_bytes, st);
   if (o.algo != DFA_ALGO_MOORE) return run_naive_minimise(d, o, block_out, res, workspace, ws_bytes, st);
 
   const bool hd = d->k > 0 && !is_device_ptr(d->delta);

@@ -39,6 +39,8 @@ int status_from_ctrl(const Ctrl &c);
 
 // naivePR / transPR (naive.cu)
 size_t naive_workspace_size(const dfa_t *d, const dfa_opts &o);
+int run_closure(const uint32_t *delta_dev, uint32_t n, uint32_t k, uint32_t *dT, Ctrl *ctrl_dev, const dfa_opts &o,
+                cudaStream_t st, Ctrl *ctrl_host);
 int run_naive_minimise(const dfa_t *d, const dfa_opts &o, uint32_t *block_out, dfa_result *res, void *workspace,
                        size_t ws_bytes, cudaStream_t st);
 

@@ -239,11 +239,10 @@ __device__ __forceinline__ void batch_filter_f(const BatchArgs &A, uint32_t *__r
 }
 
 // Pass D over the block's list: the listed states left insert their exact
-// keys into their own DFA's table region (lanes may hold different DFAs: each
-// lane inserts alone), in as many stages as the DFA's plan has (stage s tagged
-// with epoch epoch0 + s, the epoch of the round's table stage s; other DFAs'
-// table stages use other regions), and each final slot keeps its smallest
-// member (atomicMax on (round, ~local state)).
+// keys into their own DFA's table region, tagged with the round's stage-0
+// epoch (lanes may hold different DFAs: each lane inserts alone); a signature
+// wider than one key goes in as its hash, joined only on a full comparison.
+// Each slot keeps its smallest member (atomicMax on (round, ~local state)).
 __device__ __forceinline__ void batch_filter_d(const BatchArgs &A, const uint32_t *__restrict__ src, uint32_t r,
                                               uint32_t epoch0, const uint32_t *list, const uint32_t *list3,
                                               uint32_t nd) {
@@ -255,28 +254,21 @@ __device__ __forceinline__ void batch_filter_d(const BatchArgs &A, const uint32_
     const uint32_t q = gq - S.state_off, w = A.ss[list3[i] * SS_WORDS + SS_W];
     const uint32_t *lsrc = src + S.state_off;
     const StagePlan P = make_plan(S.k, w, S.log2S);
-    const uint32_t total = S.k + 1, mask = table_mask(S.log2S);
+    const uint32_t mask = table_mask(S.log2S);
     uint32_t slot[1] = {0u};
-    for (uint32_t st = 0; st < P.stages; ++st) {
+    if (P.stages == 1) {   // the whole signature is one exact key
       u128 key[1] = {u128{0ull, 0ull}};
-      uint32_t shift = 0, cbeg, cend;
-      if (st == 0) {
-        cbeg = 0;
-        cend = P.first < total ? P.first : total;
-      } else {
-        put_bits(key[0], slot[0], 0);
-        shift = P.carry;
-        cbeg = P.first + (st - 1) * P.per;
-        cend = cbeg + P.per < total ? cbeg + P.per : total;
-      }
-      for (uint32_t j = cbeg; j < cend; ++j, shift += w)
-        put_bits(key[0], j == 0 ? lsrc[q] : ld_u32_hint(lsrc + S.delta[(size_t)(j - 1) * S.n + q], keep), shift);
-      const uint32_t ep = epoch0 + st;
-      key[0].hi |= (unsigned long long)ep << (64 - A.ebits);
+      put_bits(key[0], lsrc[q], 0);
+      for (uint32_t a = 0; a < S.k; ++a)
+        put_bits(key[0], ld_u32_hint(lsrc + S.delta[(size_t)a * S.n + q], keep), (a + 1) * w);
+      key[0].hi |= (unsigned long long)epoch0 << (64 - A.ebits);
       slot[0] = (uint32_t)(mix128(key[0]) >> 32) & mask;
       const bool want[1] = {true};
       bool is_new[1];
-      table_insert_vec<1>(A.table + S.table_off, mask, key, A.ebits, ep, want, slot, is_new, &A.ctrl->err);
+      table_insert_vec<1>(A.table + S.table_off, mask, key, A.ebits, epoch0, want, slot, is_new, &A.ctrl->err);
+    } else {               // wider: signature hash plus full comparison with the slot's representative
+      const SigEq eq{lsrc, S.delta, S.n, S.k};
+      slot[0] = hashed_insert(A.table + S.table_off, mask, A.ebits, epoch0, eq.hash(q), q, eq, &A.ctrl->err);
     }
     A.tmp[gq] = slot[0];
     atomicMax(&A.rep[S.table_off + slot[0]], ((unsigned long long)r << 32) | (unsigned long long)(~q));

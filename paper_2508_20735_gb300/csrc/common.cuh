@@ -407,6 +407,53 @@ __device__ __forceinline__ void warp_insert(u128 *table, uint32_t log2S, const u
   }
 }
 
+// Signature (src[q], src[δ(q,a)] for every letter a) of a wide-key insert:
+// its 64-bit hash, and the exact comparison of two states' signatures.
+struct SigEq {
+  const uint32_t *src, *delta;
+  uint32_t n, k;
+  __device__ bool operator()(uint32_t q, uint32_t p) const {
+    if (src[q] != src[p]) return false;
+    for (uint32_t a = 0; a < k; ++a)
+      if (src[delta[(size_t)a * n + q]] != src[delta[(size_t)a * n + p]]) return false;
+    return true;
+  }
+  __device__ unsigned long long hash(uint32_t q) const {
+    unsigned long long h = hash_step(0x452821E638D01377ull, src[q]);
+    for (uint32_t a = 0; a < k; ++a) h = hash_step(h, src[delta[(size_t)a * n + q]]);
+    h ^= h >> 31;
+    h *= 0x94D049BB133111EBull;
+    return h ^ (h >> 29);
+  }
+};
+
+// Exact insert of a signature too wide for one key: the entry is (h, tag |
+// representative state), h a 64-bit hash of the signature.  An entry with the
+// same h joins q to its block only if eq(q, representative) finds the two full
+// signatures equal; otherwise probing goes on, so a hash collision never
+// merges blocks.  Entries whose tag (top tagbits bits of .hi) differs from
+// `tag` are free.  Returns q's slot; on a full table sets ERR_TABLE_FULL.
+template <class Eq>
+__device__ uint32_t hashed_insert(u128 *table, uint32_t mask, uint32_t tagbits, uint32_t tag, unsigned long long h,
+                                  uint32_t q, const Eq &eq, uint32_t *err) {
+  const uint32_t eshift = 64u - tagbits;
+  const u128 mine{h, ((unsigned long long)tag << eshift) | q};
+  uint32_t slot = (uint32_t)(h >> 32) & mask;
+  for (uint64_t iter = 0; iter <= 2ull * ((uint64_t)mask + 1); ++iter) {
+    u128 cur = ld_b128_weak(table + slot);
+    if ((uint32_t)(cur.hi >> eshift) != tag) {   // free: claim it
+      const u128 old = cas_b128(table + slot, cur, mine);
+      if (eq128(old, cur)) return slot;
+      cur = old;
+      if ((uint32_t)(cur.hi >> eshift) != tag) continue;   // replaced by another stale value: retry
+    }
+    if (cur.lo == h && eq(q, (uint32_t)cur.hi)) return slot;
+    slot = (slot + 1u) & mask;
+  }
+  atomicOr(err, ERR_TABLE_FULL);
+  return slot;
+}
+
 // ----------------------------------------------------------------- reductions / scans
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   const uint32_t lane = threadIdx.x & 31u;

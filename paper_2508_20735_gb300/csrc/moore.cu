@@ -441,6 +441,19 @@ __device__ __forceinline__ void filter_pass_d(const MooreArgs &A, uint32_t w, co
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t *list = A.dups + (size_t)gwarp * dup_cap(A.n, nwarps);
   const uint32_t nd = A.wcnt[gwarp];
+  if ((uint64_t)(A.k + 1) * w > 125) {
+    // wide signatures: each lane inserts (signature hash, state) alone; equal
+    // hashes join only if the full signatures are equal
+    const SigEq eq{src, A.delta, A.n, A.k};
+    const uint32_t mask = table_mask(m);
+    for (uint32_t i = lane; i < nd; i += 32) {
+      const uint32_t q = list[i];
+      const uint32_t slot = hashed_insert(A.table, mask, A.ebits, kFilterTag, eq.hash(q), q, eq, &A.ctrl->err);
+      A.tmp[q] = slot;
+      atomicMax(&A.rep[slot], ((unsigned long long)r << 32) | (unsigned long long)(~q));
+    }
+    return;
+  }
   for (uint32_t base = 0; base < nd; base += 32) {
     const uint32_t i = base + lane;
     const bool valid = i < nd;
@@ -539,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
     const uint64_t K = (uint64_t)(A.k + 1) * w;
     uint32_t mode = MODE_TABLE;
     if ((A.modes & 1u) && K <= A.log2S && K <= 27) mode = MODE_DIRECT;
-    else if ((A.modes & 2u) && filter_ok && !round1 && K <= 125 && (uint64_t)B_prev * 64 >= A.n) mode = MODE_FILTER;
+    else if ((A.modes & 2u) && filter_ok && !round1 && (uint64_t)B_prev * 64 >= A.n) mode = MODE_FILTER;
     if (mode == MODE_TABLE && !table_clean) {   // first table round: the table starts clean
       clear_table(A.table, A.log2S);
       ok = grid_sync(C, A.barrier_ns);

@@ -38,6 +38,61 @@ struct NaiveArgs {
   unsigned long long timeout_ns, barrier_ns;
 };
 
+// Validates δ (targets < n; a bad one sets ERR_BAD_DELTA and reads as 0) and,
+// with a closure table, copies it to level 0: row a*(L+1) holds δ(., a).
+__device__ __forceinline__ void validate_delta(const uint32_t *delta, uint32_t n, uint32_t k, uint32_t *dT,
+                                               uint32_t L, Ctrl *C) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const uint64_t kn = (uint64_t)k * n;
+  for (uint64_t i = tid; i < kn; i += stride) {
+    uint32_t t = delta[i];
+    if (t >= n) {
+      atomicOr(&C->err, ERR_BAD_DELTA);
+      t = 0;
+    }
+    if (dT) {
+      const uint32_t a = (uint32_t)(i / n), q = (uint32_t)(i % n);
+      dT[((size_t)a * (L + 1)) * n + q] = t;
+    }
+  }
+}
+
+// Closure levels 1..L by pointer doubling, one grid-wide step per level:
+// δT(q, a^(2^i)) = δT(δT(q, a^(2^(i-1))), a^(2^(i-1))).  Level 0 must have been
+// written by this launch; returns false if a barrier failed.
+__device__ __forceinline__ bool closure_levels(uint32_t n, uint32_t k, uint32_t *dT, uint32_t L, Ctrl *C,
+                                               unsigned long long barrier_ns) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const uint64_t kn = (uint64_t)k * n;
+  for (uint32_t lvl = 1; lvl <= L; ++lvl) {
+    // level lvl-1 (and the level-0 copy) must be complete everywhere
+    if (!grid_sync(C, barrier_ns)) return false;
+    for (uint64_t i = tid; i < kn; i += stride) {
+      const uint32_t a = (uint32_t)(i / n), q = (uint32_t)(i % n);
+      const uint32_t *prev = dT + ((size_t)a * (L + 1) + lvl - 1) * n;
+      dT[((size_t)a * (L + 1) + lvl) * n + q] = prev[prev[q]];
+    }
+  }
+  return true;
+}
+
+// The closure table alone (Algorithm 5's δT), for signature refinement on the
+// extended DFA.
+__global__ void __launch_bounds__(kNaiveThreads) closure_kernel(const uint32_t *delta, uint32_t n, uint32_t k,
+                                                                uint32_t *dT, uint32_t L, Ctrl *C,
+                                                                unsigned long long timeout_ns,
+                                                                unsigned long long barrier_ns) {
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  if (leader) {
+    const unsigned long long t = gtimer();
+    C->t_start = t;
+    C->deadline = t + timeout_ns;
+  }
+  validate_delta(delta, n, k, dT, L, C);
+  if (closure_levels(n, k, dT, L, C, barrier_ns)) grid_sync(C, barrier_ns);
+  if (leader) C->t_end = gtimer();
+}
+
 __global__ void __launch_bounds__(kNaiveThreads) naive_kernel(NaiveArgs A) {
   __shared__ uint32_t s_red[kNaiveThreads / 32];
   Ctrl *C = A.ctrl;
@@ -57,18 +112,7 @@ __global__ void __launch_bounds__(kNaiveThreads) naive_kernel(NaiveArgs A) {
   const uint32_t *T = A.dT ? A.dT : A.delta;
 
   // --- validate δ (and copy it to closure level 0); reset new_leader
-  const uint64_t kn = (uint64_t)k * n;
-  for (uint64_t i = tid; i < kn; i += stride) {
-    uint32_t t = A.delta[i];
-    if (t >= n) {
-      atomicOr(&C->err, ERR_BAD_DELTA);
-      t = 0;
-    }
-    if (A.dT) {
-      const uint32_t a = (uint32_t)(i / n), q = (uint32_t)(i % n);
-      A.dT[((size_t)a * (A.L + 1)) * n + q] = t;
-    }
-  }
+  validate_delta(A.delta, n, k, A.dT, A.L, C);
   for (uint32_t q = tid; q < n; q += stride) {
     A.nl[0][q] = kNone;
     A.nl[1][q] = kNone;
@@ -89,19 +133,8 @@ __global__ void __launch_bounds__(kNaiveThreads) naive_kernel(NaiveArgs A) {
       }
     }
   }
-  // --- closure levels: δT(q, a^(2^i)) = δT(δT(q, a^(2^(i-1))), a^(2^(i-1)))
-  if (A.dT) {
-    for (uint32_t lvl = 1; ok && lvl <= A.L; ++lvl) {
-      // level lvl-1 (and the level-0 copy) must be complete everywhere
-      ok = grid_sync(C, A.barrier_ns);
-      if (!ok) break;
-      for (uint64_t i = tid; i < kn; i += stride) {
-        const uint32_t a = (uint32_t)(i / n), q = (uint32_t)(i % n);
-        const uint32_t *prev = A.dT + ((size_t)a * (A.L + 1) + lvl - 1) * n;
-        A.dT[((size_t)a * (A.L + 1) + lvl) * n + q] = prev[prev[q]];
-      }
-    }
-  }
+  // --- closure levels (transPR)
+  if (ok && A.dT) ok = closure_levels(n, k, A.dT, A.L, C, A.barrier_ns);
   if (ok) ok = grid_sync(C, A.barrier_ns);
   if (ok) {
     const uint32_t qf = ld_relaxed(&C->qf), qn = ld_relaxed(&C->qn);
@@ -295,6 +328,32 @@ int run_naive_minimise(const dfa_t *d, const dfa_opts &o, uint32_t *block_out, d
     if (e != cudaSuccess) return cuda_fail(e, "copy blocks to host");
   }
   return status;
+}
+
+// Builds the closure table of a device-resident DFA into dT (k * (L+1) rows of
+// n, L = floor(log2 n)); fills *ctrl_host (ERR_BAD_DELTA for a target >= n).
+int run_closure(const uint32_t *delta_dev, uint32_t n, uint32_t k, uint32_t *dT, Ctrl *ctrl_dev, const dfa_opts &o,
+                cudaStream_t st, Ctrl *ctrl_host) {
+  const uint32_t L = (uint32_t)(63 - __builtin_clzll((unsigned long long)n));
+  cudaError_t e = cudaMemsetAsync(ctrl_dev, 0, sizeof(Ctrl), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ctrl)");
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return cuda_fail(e, "device attribute");
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, closure_kernel, kNaiveThreads, 0)) != cudaSuccess)
+    return cuda_fail(e, "occupancy");
+  const int grid = sms * (per_sm < 1 ? 1 : per_sm);
+  if ((size_t)grid > kMaxGridN) return fail(DFA_ECUDA, "grid too large");
+  unsigned long long timeout_ns = o.timeout_ns;
+  unsigned long long barrier_ns = o.timeout_ns < 5000000000ull ? o.timeout_ns : 5000000000ull;
+  void *params[] = {&delta_dev, &n, &k, &dT, const_cast<uint32_t *>(&L), &ctrl_dev, &timeout_ns, &barrier_ns};
+  e = cudaLaunchCooperativeKernel((const void *)closure_kernel, dim3(grid), dim3(kNaiveThreads), params, 0, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the closure kernel");
+  e = cudaMemcpyAsync(ctrl_host, ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "closure kernel");
+  return DFA_OK;
 }
 
 }  // namespace dfa

@@ -329,8 +329,8 @@ __device__ __forceinline__ void serve_filter_f(const StepArgs &A, const ServeSeg
 }
 
 // Pass D over a tile's listed slice: the states left insert their exact keys
-// (stage s of the plan tagged epoch0 + s) and each final slot keeps its
-// smallest member.
+// (tagged with the round's epoch; a signature wider than one key as its hash,
+// joined only on a full comparison) and each slot keeps its smallest member.
 __device__ __forceinline__ void serve_filter_d(const StepArgs &A, const ServeSeg &S, const ServeTile &T, uint32_t t) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t *list = S.list + T.start;
@@ -338,31 +338,23 @@ __device__ __forceinline__ void serve_filter_d(const StepArgs &A, const ServeSeg
   const uint32_t *src = S.lab[(S.round - 1) & 1];
   const unsigned long long keep = policy_evict_last();
   const StagePlan &P = S.plan;
-  const uint32_t total = S.k + 1, mask = table_mask(S.log2S), w = S.w;
+  const uint32_t mask = table_mask(S.log2S), w = S.w;
   for (uint32_t i = lane; i < nd; i += 32) {
     const uint32_t q = list[i];
     if (q & kServeResolved) continue;
     uint32_t slot[1] = {0u};
-    for (uint32_t st = 0; st < P.stages; ++st) {
+    if (P.stages == 1) {   // the whole signature is one exact key
       u128 key[1] = {u128{0ull, 0ull}};
-      uint32_t shift = 0, cbeg, cend;
-      if (st == 0) {
-        cbeg = 0;
-        cend = P.first < total ? P.first : total;
-      } else {
-        put_bits(key[0], slot[0], 0);
-        shift = P.carry;
-        cbeg = P.first + (st - 1) * P.per;
-        cend = cbeg + P.per < total ? cbeg + P.per : total;
-      }
-      for (uint32_t j = cbeg; j < cend; ++j, shift += w)
-        put_bits(key[0], j == 0 ? src[q] : ld_u32_hint(src + S.delta[(size_t)(j - 1) * S.n + q], keep), shift);
-      const uint32_t ep = S.epoch0 + st;
-      key[0].hi |= (unsigned long long)ep << (64 - S.ebits);
+      put_bits(key[0], src[q], 0);
+      for (uint32_t a = 0; a < S.k; ++a) put_bits(key[0], ld_u32_hint(src + S.delta[(size_t)a * S.n + q], keep), (a + 1) * w);
+      key[0].hi |= (unsigned long long)S.epoch0 << (64 - S.ebits);
       slot[0] = (uint32_t)(mix128(key[0]) >> 32) & mask;
       const bool want[1] = {true};
       bool is_new[1];
-      table_insert_vec<1>(S.table, mask, key, S.ebits, ep, want, slot, is_new, &A.ctrl->err);
+      table_insert_vec<1>(S.table, mask, key, S.ebits, S.epoch0, want, slot, is_new, &A.ctrl->err);
+    } else {               // wider: signature hash plus full comparison with the slot's representative
+      const SigEq eq{src, S.delta, S.n, S.k};
+      slot[0] = hashed_insert(S.table, mask, S.ebits, S.epoch0, eq.hash(q), q, eq, &A.ctrl->err);
     }
     S.tmp[q] = slot[0];
     atomicMax(&S.rep[slot[0]], ((unsigned long long)S.round << 32) | (unsigned long long)(~q));

@@ -47,6 +47,7 @@ def _mixed():
     base = dfagen.random_dfa(300, 3, 0.5, 61)
     dfas.append(dfagen.planted_redundancy(base, 5, 2)[0])
     dfas.append(dfagen.chain_dfa(300))
+    dfas.append(dfagen.planted_redundancy(dfagen.random_dfa(200, 30, 0.5, 63), 5, 3)[0])   # wide keys, duplicates
     return dfas
 
 

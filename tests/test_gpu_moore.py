@@ -97,6 +97,18 @@ def test_planted_redundancy(g, seed):
     _assert_parity(g, P, ref)
 
 
+@pytest.mark.parametrize("k", [30, 60])
+def test_planted_wide_keys(g, k):
+    """Copies of a minimal DFA whose signatures are wider than one 125-bit key:
+    filter rounds join the copies through the hashed exact insert (signature
+    hash plus full comparison)."""
+    base = dfagen.random_dfa(400, k, 0.5, 40 + k)
+    P, origin = dfagen.planted_redundancy(base, 5, k)
+    res = _assert_parity(g, P)
+    assert res.num_blocks == base.n
+    assert np.array_equal(_gpu_moore(g, P)[0], oracle.canonical(origin))
+
+
 def test_few_targets_heavy_merging(g):
     """Targets restricted to a few states: most states are equivalent, blocks are huge."""
     n, k = 200_000, 3
