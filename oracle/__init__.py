@@ -309,6 +309,53 @@ def closure_moore(delta, accept, max_rounds: int | None = None, history: bool = 
 
 
 # ----------------------------------------------------------------------------
+# The minimal DFA itself: reachable part, quotient by the partition
+# ----------------------------------------------------------------------------
+
+def reachable(delta, start: int) -> np.ndarray:
+    """States reachable from `start` (breadth-first search), as a bool array."""
+    delta = np.ascontiguousarray(delta, dtype=np.uint32)
+    k, n = delta.shape
+    seen = np.zeros(n, dtype=bool)
+    seen[start] = True
+    frontier = np.array([start], dtype=np.int64)
+    while frontier.size:
+        nxt = np.unique(delta[:, frontier].reshape(-1).astype(np.int64))
+        nxt = nxt[~seen[nxt]]
+        seen[nxt] = True
+        frontier = nxt
+    return seen
+
+
+@dataclass
+class Quotient:
+    delta: np.ndarray      # (k, n') letter-major
+    accept: np.ndarray     # (n',)
+    start: int
+    n: int
+
+
+def quotient(delta, accept, start: int, block) -> Quotient:
+    """The minimal DFA A' with L(A') = L(A) (Section 2's problem statement) from
+    the coarsest partition: its states are the blocks holding a state reachable
+    from `start`, numbered in order of their smallest reachable state; a block's
+    transitions and acceptance are those of that representative."""
+    delta, accept = _prep(delta, accept)
+    block = np.asarray(block, dtype=np.int64)
+    reach = reachable(delta, start)
+    states = np.nonzero(reach)[0]                       # ascending
+    blocks_in_order, first = np.unique(block[states], return_index=True)
+    reps = states[first]                                # smallest reachable state of each block
+    order = np.argsort(reps, kind="stable")
+    reps = reps[order]
+    newid = np.full(int(block.max()) + 1, -1, dtype=np.int64)
+    newid[block[reps]] = np.arange(reps.size)
+    qd = newid[block[delta[:, reps].astype(np.int64)]]
+    assert (qd >= 0).all()
+    return Quotient(qd.astype(np.uint32), accept[reps].copy(), int(newid[block[start]]), int(reps.size))
+
+
+# ----------------------------------------------------------------------------
 # Equivalence (Section 4): refine the disjoint union
 # ----------------------------------------------------------------------------
 

@@ -389,3 +389,56 @@ def test_closure_moore_fig1_first_round():
     C = dfagen.fig1_chain()
     r = oracle.closure_moore(C.delta, C.accept, history=True)
     assert r.history[1][0] != r.history[1][1]
+
+
+# ---------------------------------------------------------------- quotient (the minimal DFA itself)
+
+def test_reachable_small_cases():
+    """Hand-made graphs: the chain reaches every state from anywhere (b leads to
+    0); two separate components stay separate."""
+    C = dfagen.chain_dfa(6)
+    assert oracle.reachable(C.delta, 0).all()
+    assert oracle.reachable(C.delta, 5).all()                           # b leads back to 0
+    d = np.array([[1, 1, 3, 3]], dtype=np.uint32)                       # 0->1->1; 2->3->3
+    assert oracle.reachable(d, 0).tolist() == [True, True, False, False]
+    assert oracle.reachable(d, 2).tolist() == [False, False, True, True]
+
+
+def test_quotient_of_minimal_reachable_dfa_is_itself():
+    """All states reachable and pairwise inequivalent: the quotient is the DFA
+    with identical numbering (each block is a singleton numbered by its state)."""
+    A = dfagen.fibonacci_dfa(12)          # a unary cycle: every state reachable, minimal (Table 2)
+    blk = oracle.hopcroft(A.delta, A.accept)
+    assert blk.max() + 1 == A.n and oracle.reachable(A.delta, A.start).all()
+    Q = oracle.quotient(A.delta, A.accept, A.start, blk)
+    assert Q.n == A.n and Q.start == A.start
+    assert np.array_equal(Q.delta, A.delta) and np.array_equal(Q.accept, A.accept)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_quotient_is_minimal_and_equivalent(seed):
+    """Same language (Hopcroft-Karp), no two states equivalent (Hopcroft), every
+    state reachable, and unreachable junk dropped."""
+    A, B, _ = dfagen.equivalence_pair(seed, 9, n_lo=30, n_hi=400)
+    for X in (A, B):
+        blk = oracle.moore(X.delta, X.accept).block
+        Q = oracle.quotient(X.delta, X.accept, X.start, blk)
+        assert oracle.hk_equivalent(Q.delta, Q.accept, Q.start, X.delta, X.accept, X.start)
+        assert oracle.hopcroft(Q.delta, Q.accept).max() + 1 == Q.n
+        assert oracle.reachable(Q.delta, Q.start).all()
+        assert Q.n <= int(oracle.reachable(X.delta, X.start).sum())
+    # B is a renamed copy of A plus junk: the same minimal DFA up to renaming
+    QA = oracle.quotient(A.delta, A.accept, A.start, oracle.moore(A.delta, A.accept).block)
+    QB = oracle.quotient(B.delta, B.accept, B.start, oracle.moore(B.delta, B.accept).block)
+    if oracle.hk_equivalent(A.delta, A.accept, A.start, B.delta, B.accept, B.start):
+        assert QA.n == QB.n
+
+
+def test_quotient_planted_redundancy():
+    """Copies of a minimal DFA collapse onto it: the quotient has the base's size."""
+    base = dfagen.random_dfa(200, 3, 0.5, 72)
+    P, origin = dfagen.planted_redundancy(base, 4, 5)
+    Q = oracle.quotient(P.delta, P.accept, P.start, oracle.canonical(origin))
+    reach_base = int(oracle.reachable(base.delta, base.start).sum())
+    assert Q.n == reach_base
+    assert oracle.hk_equivalent(Q.delta, Q.accept, Q.start, base.delta, base.accept, base.start)
