@@ -160,6 +160,25 @@ int dfa_minimise_batch_packed(uint32_t count, const uint32_t *n, const uint32_t 
                               const uint8_t *accept, const dfa_opts *opts, uint32_t *block_out, dfa_result *res,
                               void *workspace, size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------- the minimal DFA */
+
+/* Workspace bytes for dfa_quotient on these arrays (0 on bad arguments). */
+size_t dfa_quotient_workspace_size(const dfa_t *d, const uint32_t *block, const uint32_t *delta_out,
+                                   const uint8_t *accept_out);
+
+/* The minimal DFA A' with L(A') = L(A) (the paper's problem statement), from a
+ * coarsest partition `block` of d's states (n entries, ids < n, as
+ * dfa_minimise writes it): A''s states are the blocks that hold a state
+ * reachable from d->start, numbered in order of their smallest reachable
+ * state; each takes the transitions and acceptance of that state.  Outputs,
+ * caller-owned, host or device: delta_out (capacity k*n; A''s letter-major
+ * table, row a at offset a*n'), accept_out (capacity n), *n_out = n' and
+ * *start_out (host).  Reachability runs on the device (breadth-first, one
+ * launch).  DFA_EINVAL for a target or block id >= n.  Synchronises the
+ * stream. */
+int dfa_quotient(const dfa_t *d, const uint32_t *block, uint32_t *delta_out, uint8_t *accept_out, uint32_t *n_out,
+                 uint32_t *start_out, void *workspace, size_t ws_bytes, void *stream);
+
 /* ---------------------------------------------------------------- equivalence */
 
 /* Workspace bytes for dfa_equivalent on this pair. */

@@ -80,6 +80,9 @@ _SIGS = [
     ("dfa_serve_stats", c_int, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
     ("dfa_serve_destroy", c_int, [c_void_p]),
     ("dfa_minimise_noalloc", c_int, [POINTER(DfaT), POINTER(DfaOpts), c_void_p, POINTER(DfaResult), c_void_p]),
+    ("dfa_quotient_workspace_size", c_size_t, [POINTER(DfaT), c_void_p, c_void_p, c_void_p]),
+    ("dfa_quotient", c_int, [POINTER(DfaT), c_void_p, c_void_p, c_void_p, POINTER(c_uint32), POINTER(c_uint32),
+                             c_void_p, c_size_t, c_void_p]),
     ("dfa_probe_l2_gather", c_int, [c_void_p, c_size_t, c_uint64, c_void_p, POINTER(c_double)]),
     ("dfa_last_error", ctypes.c_char_p, []),
     ("dfa_version", ctypes.c_char_p, []),
@@ -365,6 +368,36 @@ def minimise_batch_packed(n, k, delta, accept, algo="moore", max_rounds=0, timeo
     if check and st != DFA_OK:
         raise DfaError(st, last_error())
     return out, res
+
+
+def quotient(delta, accept, start, block, workspace=None, stream=None):
+    """The minimal DFA from a partition (dfa_quotient).  Returns (delta', accept',
+    start') as arrays of the inputs' kind (numpy in, numpy out; torch in, torch
+    out), delta' of shape (k, n')."""
+    d, keep = make_dfa(delta, accept, start)
+    blk = _contig(block, np.uint32)
+    torch_in = hasattr(keep[0], "data_ptr")
+    n, k = d.n, d.k
+    if torch_in:
+        import torch
+        dev = keep[1].device
+        dout = torch.empty(max(k * n, 1), dtype=torch.int32, device=dev)
+        aout = torch.empty(n, dtype=torch.uint8, device=dev)
+    else:
+        dout = np.empty(max(k * n, 1), dtype=np.uint32)
+        aout = np.empty(n, dtype=np.uint8)
+    need = lib().dfa_quotient_workspace_size(ctypes.byref(d), _ptr(blk), _ptr(dout), _ptr(aout))
+    if need == 0:
+        raise DfaError(DFA_EINVAL, last_error() or "bad arguments")
+    if workspace is None:
+        workspace = _workspace(need)
+    nq, sq = c_uint32(0), c_uint32(0)
+    st = lib().dfa_quotient(ctypes.byref(d), _ptr(blk), _ptr(dout), _ptr(aout), ctypes.byref(nq), ctypes.byref(sq),
+                            _ptr(workspace), int(workspace.numel()), _stream(stream))
+    if st != DFA_OK:
+        raise DfaError(st, last_error())
+    m = nq.value
+    return dout[:k * m].reshape(k, m), aout[:m], sq.value
 
 
 def probe_l2_gather(table, reads: int = 1 << 28, stream=None) -> float:
