@@ -244,6 +244,27 @@ def extras(g):
         "moore": {"rounds_needed": C.n - 1, "rounds_timed": mo.rounds_executed, "us_per_round": us_round,
                   "projected_s_for_all_rounds": us_round * (C.n - 1) / 1e6},
     }
+    # the minimal DFA itself (reachability + quotient) of the 2^24-state workload, from its partition
+    R = dfagen.random_dfa(WORKLOAD["n"], WORKLOAD["k"], WORKLOAD["p_accept"], WORKLOAD["seed"])
+    rd, ra = _dev(R)
+    blk, _ = g.minimise(rd, ra)
+    g.quotient(rd, ra, R.start, blk)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    qd, qa, qs = g.quotient(rd, ra, R.start, blk)
+    out["quotient_n2p24_k4"] = {"ms": (time.perf_counter() - t) * 1e3, "states_in": R.n, "states_out": int(qa.numel())}
+    del rd, ra, blk, qd, qa
+    # signature refinement on the closure DFA against transPR (naivePR on the same closure)
+    cm = {}
+    for name, X in (("fibonacci_n121393", dfagen.fibonacci_dfa(25)), ("chain_n2p20", C)):
+        d, a = _dev(X)
+        row = {}
+        for algo in ("closure_moore", "trans"):
+            g.minimise(d, a, algo=algo)
+            r = g.minimise(d, a, algo=algo)[1]
+            row[algo] = {"device_ms": r.device_ns / 1e6, "rounds": r.rounds_executed, "blocks": r.num_blocks}
+        cm[name] = row
+    out["closure_moore_vs_trans"] = cm
     # batch of 4,096 DFAs: one launch vs one dfa_minimise per DFA
     dfas = dfagen.batch_dfas(4096, 64, 65_536, 2, 8, 0.3, 4)
     items = [_dev(X) for X in dfas]
