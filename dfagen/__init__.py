@@ -239,6 +239,24 @@ def fig1_chain() -> DFA:
     return DFA(delta, accept, 0)
 
 
+def memory_dfa(n: int, forgetful: bool = False) -> DFA:
+    """memory_n (Section 5.1): states are the last n bits read (state s = the
+    bitstring, most significant bit first), 0...0 initial, accepting iff the
+    most significant bit is 1; reading bit b appends it and drops the most
+    significant bit.  The forgetful variant resets all bits (state b) when the
+    two most significant bits are 10."""
+    N = 1 << n
+    s = np.arange(N, dtype=np.int64)
+    rows = []
+    for b in (0, 1):
+        t = ((s << 1) | b) & (N - 1)
+        if forgetful and n >= 2:
+            t = np.where((s >> (n - 2)) == 0b10, b, t)
+        rows.append(t)
+    accept = ((s >> (n - 1)) & 1).astype(np.uint8)
+    return DFA(np.stack(rows).astype(np.uint32), accept, 0)
+
+
 def planted_redundancy(base: DFA, max_copies: int, seed: int, instance: int = 0):
     """Blow every state s of `base` up into c_s in [1, max_copies] copies.
 

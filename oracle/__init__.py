@@ -418,6 +418,52 @@ def equivalent(dA, accA, sA, dB, accB, sB, early_exit: bool = False,
 
 
 # ----------------------------------------------------------------------------
+# Product exploration (Section 4): the naive Hopcroft-Karp variant
+# ----------------------------------------------------------------------------
+
+@dataclass
+class ProductResult:
+    holds: bool            # L(A) = L(B) (equivalence) or L(A) ⊆ L(B) (inclusion)
+    pairs: int             # state pairs explored (all reachable ones if `holds`)
+    cex_len: int           # breadth-first level of a first violating pair (a shortest
+                           # counterexample's length); -1 if `holds`
+
+
+def product_explore(dA, accA, sA, dB, accB, sB, inclusion: bool = False) -> ProductResult:
+    """Algorithm 6 without R+: the set R of explored state pairs grows from
+    <q0A, q0B> by following every letter in both DFAs at once, breadth first; a
+    pair with exactly one accepting state (equivalence), or with the first
+    accepting and the second not (inclusion, the condition of Section 4's
+    variant), ends the search with `False` once its level is complete."""
+    dA, accA = _prep(dA, accA)
+    dB, accB = _prep(dB, accB)
+    if dA.shape[0] != dB.shape[0]:
+        raise ValueError("alphabets differ")
+    k = dA.shape[0]
+    nB = np.int64(accB.shape[0])
+    def bad(p, q):
+        a, b = accA[p] != 0, accB[q] != 0
+        return (a & ~b) if inclusion else (a != b)
+    frontier = np.array([int(sA) * nB + int(sB)], dtype=np.int64)
+    seen = set(frontier.tolist())
+    total, level = 1, 0
+    while frontier.size:
+        p, q = frontier // nB, frontier % nB
+        if bad(p, q).any():
+            return ProductResult(False, total, level)
+        nxt = []
+        for a in range(k):
+            nxt.append(dA[a][p].astype(np.int64) * nB + dB[a][q].astype(np.int64))
+        cand = np.unique(np.concatenate(nxt)) if nxt else np.zeros(0, dtype=np.int64)
+        new = [c for c in cand.tolist() if c not in seen]
+        seen.update(new)
+        total += len(new)
+        frontier = np.array(new, dtype=np.int64)
+        level += 1
+    return ProductResult(True, total, -1)
+
+
+# ----------------------------------------------------------------------------
 # Independent cross-checks
 # ----------------------------------------------------------------------------
 

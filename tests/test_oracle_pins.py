@@ -442,3 +442,91 @@ def test_quotient_planted_redundancy():
     reach_base = int(oracle.reachable(base.delta, base.start).sum())
     assert Q.n == reach_base
     assert oracle.hk_equivalent(Q.delta, Q.accept, Q.start, base.delta, base.accept, base.start)
+
+
+# ---------------------------------------------------------------- product exploration (Section 4)
+
+def _memory_table():
+    rows = {}
+    with open(os.path.join(GOLDEN, "memory_inclusion.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            n, count = map(int, line.split())
+            rows[n] = count
+    return rows
+
+
+def test_memory3_generator_matches_figure():
+    """Both memory_3 DFAs edge by edge against the figure."""
+    edges = {"P": {}, "F": {}}
+    with open(os.path.join(GOLDEN, "memory3_figure.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v, src, a, dst = line.split()
+            edges[v][(int(src, 2), int(a))] = int(dst, 2)
+    for v, forgetful in (("P", False), ("F", True)):
+        M = dfagen.memory_dfa(3, forgetful)
+        assert len(edges[v]) == 16
+        for (s, a), t in edges[v].items():
+            assert M.delta[a][s] == t, (v, s, a)
+        assert M.accept.tolist() == [0, 0, 0, 0, 1, 1, 1, 1] and M.start == 0
+
+
+@pytest.mark.parametrize("n", [5, 6, 7, 8, 9, 10, 11, 12])
+def test_memory_inclusion_table(n):
+    """Inclusion table: forgetful memory_n is included in perfect memory_n, and
+    the explored product has the printed state count."""
+    F, P = dfagen.memory_dfa(n, True), dfagen.memory_dfa(n, False)
+    r = oracle.product_explore(F.delta, F.accept, F.start, P.delta, P.accept, P.start, inclusion=True)
+    assert r.holds and r.cex_len == -1
+    assert r.pairs == _memory_table()[n]
+
+
+def test_memory_reverse_inclusion_fails():
+    """Perfect memory remembers more: it accepts words the forgetful one rejects."""
+    for n in (3, 5, 8):
+        F, P = dfagen.memory_dfa(n, True), dfagen.memory_dfa(n, False)
+        r = oracle.product_explore(P.delta, P.accept, P.start, F.delta, F.accept, F.start, inclusion=True)
+        assert not r.holds and r.cex_len >= n
+
+
+@pytest.mark.parametrize("idx", range(5))
+def test_self_product_is_reachable_part(idx):
+    """Comparing a DFA with itself explores one pair per reachable state (the
+    equivalence table's observation that the product has the input's size)."""
+    A = [dfagen.random_dfa(300, 2, 0.5, 3), dfagen.fibonacci_dfa(9), dfagen.bit_splitter(6),
+         dfagen.chain_dfa(50), dfagen.cycle_dfa(8)][idx]
+    r = oracle.product_explore(A.delta, A.accept, A.start, A.delta, A.accept, A.start)
+    assert r.holds and r.pairs == int(oracle.reachable(A.delta, A.start).sum())
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_product_equivalence_against_hk_and_bfs(seed):
+    """Verdict = Hopcroft-Karp with union-find; a failing check stops at the
+    level of a shortest counterexample (BFS over the product in C)."""
+    A, B, _ = dfagen.equivalence_pair(seed, 12, n_lo=20, n_hi=400)
+    args = (A.delta, A.accept, A.start, B.delta, B.accept, B.start)
+    r = oracle.product_explore(*args)
+    assert r.holds == oracle.hk_equivalent(*args)
+    assert r.cex_len == oracle.shortest_cex(*args)
+
+
+def _brute_included(A, B, L):
+    """L(A) ⊆ L(B) on all words of length <= L, by enumeration."""
+    states = {(A.start, B.start)}
+    for _ in range(L + 1):
+        if any(A.accept[p] and not B.accept[q] for p, q in states):
+            return False
+        states = {(int(A.delta[a][p]), int(B.delta[a][q])) for p, q in states for a in range(A.k)}
+    return True
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_product_inclusion_brute_force(seed):
+    """Inclusion on tiny DFAs against enumeration of all words up to n_A n_B."""
+    A = dfagen.random_dfa(5, 2, 0.4, 300 + seed)
+    B = dfagen.random_dfa(4, 2, 0.6, 400 + seed)
+    r = oracle.product_explore(A.delta, A.accept, A.start, B.delta, B.accept, B.start, inclusion=True)
+    assert r.holds == _brute_included(A, B, A.n * B.n)
