@@ -194,6 +194,31 @@ size_t dfa_equivalent_workspace_size(const dfa_t *a, const dfa_t *b, const dfa_o
 int dfa_equivalent(const dfa_t *a, const dfa_t *b, const dfa_opts *opts, int *equivalent,
                    dfa_result *res, void *workspace, size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------- product exploration */
+
+#define DFA_CHECK_EQUIVALENCE 0   /* L(A) = L(B) */
+#define DFA_CHECK_INCLUSION 1     /* L(A) ⊆ L(B) */
+
+/* Workspace bytes for dfa_product_check (0 on bad arguments). */
+size_t dfa_product_workspace_size(const dfa_t *a, const dfa_t *b, uint64_t max_pairs);
+
+/* Equivalence or inclusion by exploring the synchronous product from
+ * <start_A, start_B> (Section 4: Algorithm 6 without R+, the "naive"
+ * Hopcroft-Karp variant; inclusion drops the second disjunct of its l.5
+ * condition).  Requires k_A = k_B.  The search is breadth first on the device;
+ * a violating pair ends it once its level is complete.  Outputs (host):
+ *   *holds    1 if the condition holds, else 0;
+ *   *pairs    pairs explored: all reachable pairs if it holds, else those of
+ *             the levels up to the violating one (NULL to skip);
+ *   *cex_len  that level, the length of a shortest word in L(A) \ L(B) (or in
+ *             their symmetric difference), -1 if it holds (NULL to skip).
+ * max_pairs bounds the explored pairs (capped at n_A n_B) and sizes the
+ * workspace (8 B per pair for each of two frontiers, 16 B per pair of set);
+ * DFA_ENOMEM if the product has more reachable pairs.  Arrays may be host or
+ * device memory.  Synchronises the stream. */
+int dfa_product_check(const dfa_t *a, const dfa_t *b, int mode, uint64_t max_pairs, int *holds, uint64_t *pairs,
+                      int64_t *cex_len, void *workspace, size_t ws_bytes, void *stream);
+
 /* ---------------------------------------------------------------- serving */
 
 typedef struct dfa_server dfa_server;

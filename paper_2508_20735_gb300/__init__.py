@@ -80,6 +80,9 @@ _SIGS = [
     ("dfa_serve_stats", c_int, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
     ("dfa_serve_destroy", c_int, [c_void_p]),
     ("dfa_minimise_noalloc", c_int, [POINTER(DfaT), POINTER(DfaOpts), c_void_p, POINTER(DfaResult), c_void_p]),
+    ("dfa_product_workspace_size", c_size_t, [POINTER(DfaT), POINTER(DfaT), c_uint64]),
+    ("dfa_product_check", c_int, [POINTER(DfaT), POINTER(DfaT), c_int, c_uint64, POINTER(c_int), POINTER(c_uint64),
+                                  POINTER(ctypes.c_int64), c_void_p, c_size_t, c_void_p]),
     ("dfa_quotient_workspace_size", c_size_t, [POINTER(DfaT), c_void_p, c_void_p, c_void_p]),
     ("dfa_quotient", c_int, [POINTER(DfaT), c_void_p, c_void_p, c_void_p, POINTER(c_uint32), POINTER(c_uint32),
                              c_void_p, c_size_t, c_void_p]),
@@ -368,6 +371,34 @@ def minimise_batch_packed(n, k, delta, accept, algo="moore", max_rounds=0, timeo
     if check and st != DFA_OK:
         raise DfaError(st, last_error())
     return out, res
+
+
+DFA_CHECK_EQUIVALENCE = 0
+DFA_CHECK_INCLUSION = 1
+
+
+def product_check(A, B, inclusion=False, max_pairs=None, workspace=None, stream=None):
+    """Equivalence (or inclusion L(A) ⊆ L(B)) by product exploration
+    (dfa_product_check).  A and B are (delta, accept, start) triples.  Returns
+    (holds, pairs explored, counterexample length or -1).  max_pairs bounds the
+    explored pairs (default min(n_A n_B, 8 (n_A + n_B) + 65536)); a larger
+    product raises DfaError(DFA_ENOMEM)."""
+    a, ka = make_dfa(A[0], A[1], A[2])
+    b, kb = make_dfa(B[0], B[1], B[2])
+    if max_pairs is None:
+        max_pairs = min(a.n * b.n, 8 * (a.n + b.n) + 65536)
+    need = lib().dfa_product_workspace_size(ctypes.byref(a), ctypes.byref(b), int(max_pairs))
+    if need == 0:
+        raise DfaError(DFA_EINVAL, last_error() or "bad arguments")
+    if workspace is None:
+        workspace = _workspace(need)
+    holds, pairs, cex = c_int(0), c_uint64(0), ctypes.c_int64(0)
+    st = lib().dfa_product_check(ctypes.byref(a), ctypes.byref(b), DFA_CHECK_INCLUSION if inclusion else
+                                 DFA_CHECK_EQUIVALENCE, int(max_pairs), ctypes.byref(holds), ctypes.byref(pairs),
+                                 ctypes.byref(cex), _ptr(workspace), int(workspace.numel()), _stream(stream))
+    if st != DFA_OK:
+        raise DfaError(st, last_error())
+    return bool(holds.value), int(pairs.value), int(cex.value)
 
 
 def quotient(delta, accept, start, block, workspace=None, stream=None):
