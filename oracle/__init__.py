@@ -16,6 +16,8 @@ Definition-level functions (numpy; a library sort is the only primitive):
   * :func:`closure`    the partial transitive closure δT (Section 3.4,
                        Algorithm 5) by pointer doubling.
   * :func:`trans_pr`   ``transPR`` = closure, then naivePR on A' (Algorithm 5).
+  * :func:`trans`      ``trans``: transitive closure of the pair graph
+                       (Section 3.1, Algorithm 1), tiny n only.
   * :func:`equivalent` language equivalence by refining the disjoint union
                        (Section 4: equivalence via minimisation).
   * :func:`canonical`  blocks renumbered 0..B-1 in increasing order of their
@@ -306,6 +308,62 @@ def closure_moore(delta, accept, max_rounds: int | None = None, history: bool = 
     of up to 2^L letters of A at once."""
     delta, accept = _prep(delta, accept)
     return moore(closure(delta), accept, max_rounds=max_rounds, history=history, stop_discrete=stop_discrete)
+
+
+# ----------------------------------------------------------------------------
+# trans: transitive closure of the pair graph (Section 3.1, Algorithm 1)
+# ----------------------------------------------------------------------------
+
+def trans_square(reach: np.ndarray) -> np.ndarray:
+    """Algorithm 1's first parallel step: Reach[s][u] := true wherever
+    Reach[s][t] and Reach[t][u] for some t (0/1 matrices)."""
+    return ((reach + reach @ reach) > 0).astype(np.float64)
+
+
+def trans_label(reach: np.ndarray, apart: np.ndarray) -> np.ndarray:
+    """Algorithm 1's second parallel step: s becomes Apart if Reach[s][t] for an
+    Apart node t."""
+    return apart | ((reach @ apart.astype(np.float64)) > 0)
+
+
+@dataclass
+class TransResult:
+    block: np.ndarray        # canonical partition: q, q' share a block iff not Apart(q, q')
+    iterations: int          # executions of the while loop, the last one labelling nothing new
+    apart: np.ndarray        # bool[n, n]
+
+
+def trans(delta, accept, max_iterations: int | None = None) -> TransResult:
+    """Algorithm 1 (trans).  The pair graph has the nodes (q, q') in Q x Q,
+    numbered q*n + q', and an edge (q, q') -> (δ(q,a), δ(q',a)) for every
+    letter a; Apart starts with the pairs on which F disagrees.  Each iteration
+    of the while loop (i) extends Reach by every path Reach[s][t], Reach[t][u]
+    and (ii) labels s Apart if Reach[s][t] for an Apart t; the loop ends after
+    an iteration in which (ii) labels nothing new.  Synchronous reading: each
+    parallel step reads the values from before the step, so iteration i ends
+    with Reach = paths of 1..2^i edges.  The boolean products are 0/1 matrix
+    products (a library matmul, exact: the sums stay far below 2^53)."""
+    delta, accept = _prep(delta, accept)
+    k, n = delta.shape
+    V = n * n
+    q, qp = np.divmod(np.arange(V, dtype=np.int64), n)
+    reach = np.zeros((V, V), dtype=np.float64)
+    for a in range(k):
+        reach[np.arange(V), delta[a][q].astype(np.int64) * n + delta[a][qp]] = 1.0
+    apart = accept[q] != accept[qp]
+    it = 0
+    while max_iterations is None or it < max_iterations:
+        it += 1
+        reach = trans_square(reach)
+        new = trans_label(reach, apart)
+        grew = bool((new & ~apart).any())
+        apart = new
+        if not grew:
+            break
+    A = apart.reshape(n, n)
+    rep = np.array([int(np.flatnonzero(~A[x])[0]) for x in range(n)], dtype=np.int64) if n else \
+        np.zeros(0, dtype=np.int64)
+    return TransResult(canonical(rep), it, A)
 
 
 # ----------------------------------------------------------------------------

@@ -530,3 +530,100 @@ def test_product_inclusion_brute_force(seed):
     B = dfagen.random_dfa(4, 2, 0.6, 400 + seed)
     r = oracle.product_explore(A.delta, A.accept, A.start, B.delta, B.accept, B.start, inclusion=True)
     assert r.holds == _brute_included(A, B, A.n * B.n)
+
+
+# ---------------------------------------------------------------- trans (Algorithm 1)
+
+def _trans_rows():
+    rows = {}
+    with open(os.path.join(GOLDEN, "trans_table1.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            N, it = map(int, line.split())
+            rows[N] = it
+    return rows
+
+
+def _trans_iterations_closed_form(D):
+    """Iteration i ends with Reach = paths of 1..2^i edges, so Apart then holds
+    every pair within 2^(i+1) - 2 edges of an initially Apart pair; the pairs
+    first separated by Moore's round r are exactly those at distance r, so with
+    D = the last round that splits, the loop labels something new in iterations
+    1..i* (i* the least i with 2^(i+1) - 2 >= D) and stops after i* + 1."""
+    i = 0
+    while (1 << (i + 1)) - 2 < D:
+        i += 1
+    return i + 1
+
+
+def _trans_cases():
+    yield dfagen.random_dfa(12, 2, 0.5, 1)
+    yield dfagen.random_dfa(20, 3, 0.3, 2)
+    yield dfagen.random_dfa(25, 1, 0.5, 3)
+    yield dfagen.bit_splitter(4)
+    yield dfagen.chain_dfa(16)
+    yield dfagen.cycle_dfa(9)
+    yield dfagen.planted_redundancy(dfagen.random_dfa(6, 2, 0.5, 9), 3, 1)[0]
+    yield dfagen.random_dfa(15, 2, 0.0, 4)
+
+
+@pytest.mark.parametrize("idx", range(8))
+def test_trans_partition_and_closed_form(idx):
+    """trans gives Hopcroft's partition, and its iteration count is the closed
+    form in the distance to the first Apart pair (from Moore's rounds)."""
+    A = list(_trans_cases())[idx]
+    r = oracle.trans(A.delta, A.accept)
+    assert np.array_equal(r.block, oracle.hopcroft(A.delta, A.accept))
+    D = oracle.moore(A.delta, A.accept).rounds_changed
+    assert r.iterations == _trans_iterations_closed_form(D)
+    # Apart is symmetric, irreflexive, and exactly "different blocks"
+    assert np.array_equal(r.apart, r.apart.T) and not r.apart.diagonal().any()
+    assert np.array_equal(r.apart, r.block[:, None] != r.block[None, :])
+
+
+def test_trans_table_rows():
+    """The table's iteration counts for N = 8, 13, 21 come out of the oracle; for
+    N = 55 and 89 (too large for the dense oracle) out of the closed form with
+    D = N - 2 (Moore's rounds on Fibonacci).  N = 34 is printed as 5 where the
+    synchronous reading gives 6: the paper's code updates Reach and Apart in
+    place, which can only label pairs earlier, so the printed count never
+    exceeds the synchronous one."""
+    rows = _trans_rows()
+    for N, printed in rows.items():
+        A = dfagen.fibonacci_dfa_with_states(N)
+        if N <= 21:
+            r = oracle.trans(A.delta, A.accept)
+            assert r.iterations == printed, N
+            assert len(set(r.block.tolist())) == N
+        ours = _trans_iterations_closed_form(N - 2)
+        assert printed <= ours
+        assert (printed == ours) == (N != 34), N
+
+
+def test_trans_fib34_synchronous():
+    A = dfagen.fibonacci_dfa_with_states(34)
+    r = oracle.trans(A.delta, A.accept)
+    assert r.iterations == 6 and oracle.moore(A.delta, A.accept).rounds_changed == 32
+
+
+def test_pins_catch_trans_without_squaring(monkeypatch):
+    """Leaving out the closure step makes trans a one-edge-per-iteration search,
+    which the table rows (and the closed form) catch."""
+    A = dfagen.fibonacci_dfa_with_states(21)
+    monkeypatch.setattr(oracle, "trans_square", lambda reach: reach)
+    assert oracle.trans(A.delta, A.accept).iterations != _trans_rows()[21]
+
+
+def test_pins_catch_trans_label_from_wrong_side(monkeypatch):
+    """Labelling the Apart node's predecessors through Reach transposed (t -> s
+    instead of s -> t) gives a wrong partition."""
+    A = dfagen.random_dfa(12, 2, 0.5, 1)
+    h = oracle.hopcroft(A.delta, A.accept)
+    monkeypatch.setattr(oracle, "trans_label",
+                        lambda reach, apart: apart | ((reach.T @ apart.astype(np.float64)) > 0))
+    try:
+        r = oracle.trans(A.delta, A.accept)
+    except IndexError:          # a state Apart from itself: no representative
+        return
+    assert not np.array_equal(r.block, h) or r.apart.diagonal().any() or not np.array_equal(r.apart, r.apart.T)
