@@ -253,7 +253,47 @@ def extras(g):
     t = time.perf_counter()
     qd, qa, qs = g.quotient(rd, ra, R.start, blk)
     out["quotient_n2p24_k4"] = {"ms": (time.perf_counter() - t) * 1e3, "states_in": R.n, "states_out": int(qa.numel())}
+    # the paper's renumbering (radix sort + adjacent difference + scan per round) against the hash
+    g.minimise(rd, ra, algo="sort")
+    so = g.minimise(rd, ra, algo="sort")[1]
+    ha = g.minimise(rd, ra)[1]
+    out["sort_vs_hash_n2p24_k4"] = {
+        "sort": {"device_ms": so.device_ns / 1e6, "rounds": so.rounds_executed, "blocks": so.num_blocks},
+        "hash": {"device_ms": ha.device_ns / 1e6, "rounds": ha.rounds_executed, "blocks": ha.num_blocks},
+    }
     del rd, ra, blk, qd, qa
+    # product exploration (Section 4's naive Hopcroft-Karp): the inclusion table's largest case, and a
+    # million-state equivalent pair against refinement of the union
+    F, P = dfagen.memory_dfa(15, True), dfagen.memory_dfa(15, False)
+    fd, pd_ = _dev(F) + (F.start,), _dev(P) + (P.start,)
+    g.product_check(fd, pd_, inclusion=True)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    holds, pairs, _ = g.product_check(fd, pd_, inclusion=True)
+    out["product_memory15_inclusion"] = {"ms": (time.perf_counter() - t) * 1e3, "holds": holds, "pairs": pairs}
+    EA, EB, _ = dfagen.equivalence_pair(0, 17, n_lo=1_000_000, n_hi=1_000_001, force="equivalent")
+    ea, eb = _dev(EA) + (EA.start,), _dev(EB) + (EB.start,)
+    row = {}
+    for name, call in (("product", lambda: g.product_check(ea, eb)), ("union_refinement", lambda: g.equivalent(ea, eb))):
+        call()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = call()
+        row[name] = {"ms": (time.perf_counter() - t) * 1e3, "equivalent": bool(r[0])}
+    row["states"] = [EA.n, EB.n]
+    out["equivalence_1m_product_vs_union"] = row
+    # trans (Algorithm 1): the table's largest Fibonacci DFA and two it could not run
+    row = {}
+    for N in (89, 144, 233):
+        F = dfagen.fibonacci_dfa_with_states(N)
+        fd, fa = _dev(F)
+        g.trans(fd, fa)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        blk, it = g.trans(fd, fa)
+        row[f"fibonacci_n{N}"] = {"ms": (time.perf_counter() - t) * 1e3, "iterations": it,
+                                  "blocks": int(blk.max().item()) + 1, "pair_nodes": N * N}
+    out["trans_fibonacci"] = row
     # signature refinement on the closure DFA against transPR (naivePR on the same closure)
     cm = {}
     for name, X in (("fibonacci_n121393", dfagen.fibonacci_dfa(25)), ("chain_n2p20", C)):
@@ -528,15 +568,18 @@ def main():
         dist.destroy_process_group()
 
 
+# the sources the signature-refinement kernel and its launch are compiled from
+MOORE_SOURCES = ("api.cu", "api_util.h", "common.cuh", "internal.h", "moore.cu")
+
+
 def kernel_source_hash() -> str:
-    """Hash of the kernel sources, tying a committed ncu traffic figure to the code it measured."""
+    """Hash of the refinement kernel's sources, tying a committed ncu traffic figure to the code it measured."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2508_20735_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    for f in MOORE_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 

@@ -76,7 +76,11 @@ typedef enum dfa_algo {
                                  instead of naivePR: same partition (the extra letters are words over
                                  the alphabet); rounds are those of Algorithm 4 on the extended DFA,
                                  on the n-state chain max popcount(x), 1 <= x <= n - 2, of them.  An
-                                 extension the paper leaves open (it asks for sublinear refinement). */
+                                 extension the paper leaves open (it asks for sublinear refinement). */,
+  DFA_ALGO_SORT = 4       /* Algorithm 4 with the paper's own renumbering: each round radix-sorts the
+                             states by signature, marks signature changes and scans the marks (the
+                             count read back on the host every round).  Same partition and rounds as
+                             DFA_ALGO_MOORE; kept as the sort-versus-hash comparison. */
 } dfa_algo;
 
 /* Flags for dfa_opts.flags */
@@ -204,8 +208,8 @@ size_t dfa_product_workspace_size(const dfa_t *a, const dfa_t *b, uint64_t max_p
 
 /* Equivalence or inclusion by exploring the synchronous product from
  * <start_A, start_B> (Section 4: Algorithm 6 without R+, the "naive"
- * Hopcroft-Karp variant; inclusion drops the second disjunct of its l.5
- * condition).  Requires k_A = k_B.  The search is breadth first on the device;
+ * Hopcroft-Karp variant; inclusion keeps only the "A accepts, B rejects" half
+ * of its acceptance test).  Requires k_A = k_B.  The search is breadth first on the device;
  * a violating pair ends it once its level is complete.  Outputs (host):
  *   *holds    1 if the condition holds, else 0;
  *   *pairs    pairs explored: all reachable pairs if it holds, else those of
@@ -218,6 +222,28 @@ size_t dfa_product_workspace_size(const dfa_t *a, const dfa_t *b, uint64_t max_p
  * device memory.  Synchronises the stream. */
 int dfa_product_check(const dfa_t *a, const dfa_t *b, int mode, uint64_t max_pairs, int *holds, uint64_t *pairs,
                       int64_t *cex_len, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- trans (Algorithm 1) */
+
+/* Largest n for dfa_trans: Reach has n^4 bits (two copies of 512 MiB at 256). */
+#define DFA_TRANS_MAX_STATES 256u
+
+/* Workspace bytes for dfa_trans (0 on bad arguments or n > DFA_TRANS_MAX_STATES). */
+size_t dfa_trans_workspace_size(const dfa_t *d, const uint32_t *block_out);
+
+/* Algorithm 1 (Section 3.1, "trans"): minimisation by the transitive closure
+ * of the pair graph, whose nodes are the n^2 state pairs and whose edges are
+ * (q, q') -> (δ(q,a), δ(q',a)).  Each iteration squares the boolean
+ * reachability matrix (R := R | R R) and then labels Apart every pair with an
+ * edge of R to an Apart pair; both steps read only the previous iteration's
+ * values.  The loop stops after an iteration that labels nothing new.
+ * Outputs: block_out[q] (n entries, host or device), the canonical partition
+ * (q, q' in one block iff not Apart); *iterations (host), the loop's
+ * executions including the last.  δ and accept may be host or device memory;
+ * δ entries >= n give DFA_EINVAL.  Synchronises the stream once per
+ * iteration (the loop test is read on the host). */
+int dfa_trans(const dfa_t *d, uint32_t *block_out, uint32_t *iterations, void *workspace, size_t ws_bytes,
+              void *stream);
 
 /* ---------------------------------------------------------------- serving */
 

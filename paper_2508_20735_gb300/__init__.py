@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libdfa_gb300.so")
 DFA_OK, DFA_EINVAL, DFA_ENOMEM, DFA_ECUDA, DFA_ETIMEOUT, DFA_EMAXROUNDS, DFA_EBUSY, DFA_ECANCELLED = 0, -1, -2, -3, -4, -5, -6, -7
 STATUS_NAMES = {0: "DFA_OK", -1: "DFA_EINVAL", -2: "DFA_ENOMEM", -3: "DFA_ECUDA", -4: "DFA_ETIMEOUT",
                 -5: "DFA_EMAXROUNDS", -6: "DFA_EBUSY", -7: "DFA_ECANCELLED"}
-ALGOS = {"moore": 0, "naive": 1, "trans": 2, "closure_moore": 3}
+ALGOS = {"moore": 0, "naive": 1, "trans": 2, "closure_moore": 3, "sort": 4}
 DFA_FLAG_EARLY_EXIT = 0x1
 DFA_FLAG_TABLE_ONLY = 0x2
 DFA_FLAG_STOP_DISCRETE = 0x4
@@ -86,6 +86,8 @@ _SIGS = [
     ("dfa_quotient_workspace_size", c_size_t, [POINTER(DfaT), c_void_p, c_void_p, c_void_p]),
     ("dfa_quotient", c_int, [POINTER(DfaT), c_void_p, c_void_p, c_void_p, POINTER(c_uint32), POINTER(c_uint32),
                              c_void_p, c_size_t, c_void_p]),
+    ("dfa_trans_workspace_size", c_size_t, [POINTER(DfaT), c_void_p]),
+    ("dfa_trans", c_int, [POINTER(DfaT), c_void_p, POINTER(c_uint32), c_void_p, c_size_t, c_void_p]),
     ("dfa_probe_l2_gather", c_int, [c_void_p, c_size_t, c_uint64, c_void_p, POINTER(c_double)]),
     ("dfa_last_error", ctypes.c_char_p, []),
     ("dfa_version", ctypes.c_char_p, []),
@@ -429,6 +431,32 @@ def quotient(delta, accept, start, block, workspace=None, stream=None):
         raise DfaError(st, last_error())
     m = nq.value
     return dout[:k * m].reshape(k, m), aout[:m], sq.value
+
+
+DFA_TRANS_MAX_STATES = 256
+
+
+def trans(delta, accept, workspace=None, stream=None):
+    """Algorithm 1 (dfa_trans): the partition by transitive closure of the pair
+    graph, n <= DFA_TRANS_MAX_STATES.  Returns (block, iterations), block of the
+    inputs' kind (numpy in, numpy out; torch in, torch out)."""
+    d, keep = make_dfa(delta, accept, 0)
+    if hasattr(keep[1], "data_ptr"):
+        import torch
+        out = torch.empty(d.n, dtype=torch.int32, device=keep[1].device)
+    else:
+        out = np.empty(d.n, dtype=np.uint32)
+    need = lib().dfa_trans_workspace_size(ctypes.byref(d), _ptr(out))
+    if need == 0:
+        raise DfaError(DFA_EINVAL, last_error() or "bad arguments")
+    if workspace is None:
+        workspace = _workspace(need)
+    it = c_uint32(0)
+    st = lib().dfa_trans(ctypes.byref(d), _ptr(out), ctypes.byref(it), _ptr(workspace), int(workspace.numel()),
+                         _stream(stream))
+    if st != DFA_OK:
+        raise DfaError(st, last_error())
+    return out, it.value
 
 
 def probe_l2_gather(table, reads: int = 1 << 28, stream=None) -> float:

@@ -306,6 +306,7 @@ size_t dfa_workspace_size(const dfa_t *d, const dfa_opts *opts) {
   const bool ha = !is_device_ptr(d->accept);
   if (o.algo == DFA_ALGO_MOORE) return moore_layout(d->n, d->k, hd, ha, true).total;
   if (o.algo == DFA_ALGO_CLOSURE_MOORE) return closure_moore_layout(d->n, d->k, hd, ha).total;
+  if (o.algo == DFA_ALGO_SORT) return sort_workspace_size(d, hd, ha, true);
   return naive_workspace_size(d, o);
 }
 
@@ -318,10 +319,11 @@ int dfa_minimise(const dfa_t *d, const dfa_opts *opts, uint32_t *block_out, dfa_
   if (!aligned(workspace, 256)) return fail(DFA_EINVAL, "workspace must be 256-byte aligned");
   const dfa_opts o = default_opts(opts);
   if (o.algo != DFA_ALGO_MOORE && o.algo != DFA_ALGO_NAIVE && o.algo != DFA_ALGO_TRANS &&
-      o.algo != DFA_ALGO_CLOSURE_MOORE)
+      o.algo != DFA_ALGO_CLOSURE_MOORE && o.algo != DFA_ALGO_SORT)
     return fail(DFA_EINVAL, "unknown algo %d", o.algo);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (o.algo == DFA_ALGO_CLOSURE_MOORE) return run_closure_moore(d, o, block_out, res, workspace, ws_bytes, st);
+  if (o.algo == DFA_ALGO_SORT) return run_sort_minimise(d, o, block_out, res, workspace, ws_bytes, st);
   if (o.algo != DFA_ALGO_MOORE) return run_naive_minimise(d, o, block_out, res, workspace, ws_bytes, st);
 
   const bool hd = d->k > 0 && !is_device_ptr(d->delta);

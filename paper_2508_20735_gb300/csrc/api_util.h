@@ -44,6 +44,11 @@ int run_closure(const uint32_t *delta_dev, uint32_t n, uint32_t k, uint32_t *dT,
 int run_naive_minimise(const dfa_t *d, const dfa_opts &o, uint32_t *block_out, dfa_result *res, void *workspace,
                        size_t ws_bytes, cudaStream_t st);
 
+// sortPR with radix-sort renumbering (sortpr.cu)
+size_t sort_workspace_size(const dfa_t *d, bool stage_delta, bool stage_accept, bool stage_out);
+int run_sort_minimise(const dfa_t *d, const dfa_opts &o, uint32_t *block_out, dfa_result *res, void *workspace,
+                      size_t ws_bytes, cudaStream_t st);
+
 // disjoint union helper (equiv.cu)
 cudaError_t launch_offset_targets(uint32_t *delta_u, uint32_t n_u, uint32_t k, uint32_t first, uint32_t count,
                                   uint32_t offset, uint32_t *err, cudaStream_t st);
