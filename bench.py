@@ -264,13 +264,17 @@ def extras(g):
     del rd, ra, blk, qd, qa
     # product exploration (Section 4's naive Hopcroft-Karp): the inclusion table's largest case, and a
     # million-state equivalent pair against refinement of the union
-    F, P = dfagen.memory_dfa(15, True), dfagen.memory_dfa(15, False)
-    fd, pd_ = _dev(F) + (F.start,), _dev(P) + (P.start,)
-    g.product_check(fd, pd_, inclusion=True)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    holds, pairs, _ = g.product_check(fd, pd_, inclusion=True)
-    out["product_memory15_inclusion"] = {"ms": (time.perf_counter() - t) * 1e3, "holds": holds, "pairs": pairs}
+    for m in (15, 27):
+        F, P = dfagen.memory_dfa(m, True), dfagen.memory_dfa(m, False)
+        fd, pd_ = _dev(F) + (F.start,), _dev(P) + (P.start,)
+        cap = 1 << 31 if m > 20 else None
+        g.product_check(fd, pd_, inclusion=True, max_pairs=cap)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        holds, pairs, _ = g.product_check(fd, pd_, inclusion=True, max_pairs=cap)
+        out[f"product_memory{m}_inclusion"] = {"ms": (time.perf_counter() - t) * 1e3, "holds": holds, "pairs": pairs}
+        del fd, pd_
+        torch.cuda.empty_cache()
     EA, EB, _ = dfagen.equivalence_pair(0, 17, n_lo=1_000_000, n_hi=1_000_001, force="equivalent")
     ea, eb = _dev(EA) + (EA.start,), _dev(EB) + (EB.start,)
     row = {}

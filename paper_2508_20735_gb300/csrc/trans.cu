@@ -11,9 +11,10 @@
 // parallel steps), and the loop stops after an iteration that labels nothing.
 //
 // The product is a dense contraction, but over (OR, AND) on bits: one 32-bit
-// LOP3 performs 32 boolean multiply-adds, which matches a bf16 tensor-core
-// product of 0/1 matrices in throughput at 1/16 of its memory, so the kernel
-// runs on the integer pipes with operands staged in shared memory.
+// LOP3 performs 32 boolean multiply-adds, so the packed product on the integer
+// pipe reaches about half the dense bf16 tensor-core multiply-add rate while
+// keeping Reach at one bit per entry, needing no threshold between squarings,
+// and skipping 32-column slabs that are zero in all of a tile's rows.
 #include "api_util.h"
 
 namespace dfa {
@@ -62,13 +63,16 @@ __global__ void trans_init_kernel(const uint32_t *__restrict__ delta, const uint
 // and words 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3 of that tile, so
 // the shared-memory loads of a warp are contiguous.  The contraction index t
 // runs one word (32 nodes) at a time: the tile's 64 row words of R at column
-// word tw, then rows 32 tw .. 32 tw + 31 of R restricted to the tile's words.
+// word tw, expanded once into 32 x 64 all-ones/all-zeros row masks, and rows
+// 32 tw .. 32 tw + 31 of R restricted to the tile's words, all in shared
+// memory, so the inner step is one LOP3 per accumulator word.
 // A column word that is zero in all 64 rows is skipped (R starts with k bits a
 // row).  W is a multiple of 8 and the matrix has 32 W rows, so every uint4 is
 // either wholly inside the row or wholly past its end.
 __global__ void __launch_bounds__(kSqThreads, 3) trans_square_kernel(const uint32_t *__restrict__ R,
                                                                   uint32_t *__restrict__ C, uint32_t W) {
   __shared__ uint4 bs[32][32];           // 32 rows t x 128 words
+  __shared__ uint4 ms[32][kSqRows / 4];  // ms[b] word r: all ones iff bit b of row r's column word
   __shared__ uint32_t as[kSqRows];       // the tile's rows, one column word
   const uint32_t tx = threadIdx.x & 15u, ty = threadIdx.x >> 4;
   const uint32_t row0 = blockIdx.y * kSqRows, w0 = blockIdx.x * kSqWords;
@@ -85,6 +89,13 @@ __global__ void __launch_bounds__(kSqThreads, 3) trans_square_kernel(const uint3
       as[threadIdx.x] = mine;
     }
     if (!__syncthreads_or(mine != 0)) continue;
+    {   // row masks, computed once per column word instead of once per thread
+      const uint32_t row = threadIdx.x & (kSqRows - 1), b0 = (threadIdx.x / kSqRows) * 16;
+      const uint32_t w = as[row];
+      uint32_t *mrow = reinterpret_cast<uint32_t *>(ms);
+#pragma unroll
+      for (uint32_t b = 0; b < 16; ++b) mrow[(b0 + b) * kSqRows + row] = 0u - ((w >> (b0 + b)) & 1u);
+    }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const uint32_t u = threadIdx.x + r * kSqThreads;   // uint4 index in the 32 x 32 tile
@@ -94,15 +105,14 @@ __global__ void __launch_bounds__(kSqThreads, 3) trans_square_kernel(const uint3
       bs[j][c4] = v;
     }
     __syncthreads();
-    uint32_t a[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) a[i] = as[ty * 8 + i];
 #pragma unroll
     for (int b = 0; b < 32; ++b) {
       const uint4 b0 = bs[b][tx], b1 = bs[b][16 + tx];
+      const uint4 m0 = ms[b][2 * ty], m1 = ms[b][2 * ty + 1];
+      const uint32_t mk[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const uint32_t m = (uint32_t)((int32_t)(a[i] << (31 - b)) >> 31);   // all ones iff bit b of a[i]
+        const uint32_t m = mk[i];
         acc[i][0] |= m & b0.x;
         acc[i][1] |= m & b0.y;
         acc[i][2] |= m & b0.z;

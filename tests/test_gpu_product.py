@@ -39,13 +39,26 @@ def _table():
     return rows
 
 
-@pytest.mark.parametrize("n", list(range(5, 16)))
+@pytest.mark.parametrize("n", list(range(5, 25)))
 def test_memory_inclusion_table(g, n):
-    """The inclusion table in full (memory_5 .. memory_15): holds, with the
-    printed number of explored product states."""
+    """The inclusion table (memory_5 .. memory_24): holds, with the printed
+    number of explored product states."""
     F, P = dfagen.memory_dfa(n, True), dfagen.memory_dfa(n, False)
     holds, pairs, cex = g.product_check(_dev(F), _dev(P), inclusion=True)
     assert holds and cex == -1 and pairs == _table()[n]
+
+
+@pytest.mark.parametrize("n", [25, 26, 27])
+def test_memory_inclusion_table_largest(g, n):
+    """The table's largest rows (up to 1.85e9 product states, 64 GB of search
+    state), with max_pairs set to the printed count: a larger product would
+    end with DFA_ENOMEM."""
+    import torch
+    F, P = dfagen.memory_dfa(n, True), dfagen.memory_dfa(n, False)
+    want = _table()[n]
+    holds, pairs, cex = g.product_check(_dev(F), _dev(P), inclusion=True, max_pairs=want)
+    assert holds and cex == -1 and pairs == want
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("n", [3, 6, 10])
