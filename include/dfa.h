@@ -216,7 +216,7 @@ size_t dfa_product_workspace_size(const dfa_t *a, const dfa_t *b, uint64_t max_p
  *             the levels up to the violating one (NULL to skip);
  *   *cex_len  that level, the length of a shortest word in L(A) \ L(B) (or in
  *             their symmetric difference), -1 if it holds (NULL to skip).
- * max_pairs bounds the explored pairs (capped at n_A n_B) and sizes the
+ * max_pairs bounds the explored pairs (capped at n_A n_B and 2^31) and sizes the
  * workspace (8 B per pair for each of two frontiers, 16 B per pair of set);
  * DFA_ENOMEM if the product has more reachable pairs.  Arrays may be host or
  * device memory.  Synchronises the stream. */

@@ -4,7 +4,7 @@
 // cooperative kernel of this library).
 //
 // The explored set R of state pairs is a lock-free open-addressing set of
-// 64-bit keys p * n_B + q + 1 (0 = empty).  The search is breadth first, one
+// 64-bit keys (p << 32) | q (all ones = empty: p, q < 2^31).  The search is breadth first, one
 // grid barrier per level; while a level holds at most kPLocalMax pairs, block 0
 // alone runs up to kPLocalLevels levels between grid barriers.  Every pair of a
 // level is tested before the level's expansion counts: a pair with exactly one
@@ -50,6 +50,14 @@ struct ProdArgs {
   unsigned long long timeout_ns, barrier_ns;
 };
 
+static constexpr unsigned long long kEmptyKey = ~0ull;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ unsigned long long pmix(unsigned long long x) {
   x ^= x >> 33;
   x *= 0xff51afd7ed558ccdull;
@@ -58,13 +66,19 @@ __device__ __forceinline__ unsigned long long pmix(unsigned long long x) {
 }
 
 // Inserts key into the set; true if it was not there.  A full set raises
-// ERR_TABLE_FULL (reported as DFA_ENOMEM) and returns false.
+// ERR_TABLE_FULL (reported as DFA_ENOMEM) and returns false.  A slot changes
+// once, from empty to a key, so a plain read that finds a key is final: only
+// slots read as empty take an atomic (about half the successors of a level
+// are already in the set, and atomics that miss L2 are the costly accesses).
 __device__ __forceinline__ bool set_insert(const ProdArgs &A, unsigned long long key) {
   const unsigned long long mask = (1ull << A.log2set) - 1;
   unsigned long long slot = pmix(key) & mask;
   for (unsigned long long it = 0; it <= mask; ++it) {
-    const unsigned long long old = atomicCAS(&A.set[slot], 0ull, key);
-    if (old == 0ull) return true;
+    unsigned long long old = ld_relaxed_u64(&A.set[slot]);
+    if (old == kEmptyKey) {
+      old = atomicCAS(&A.set[slot], kEmptyKey, key);
+      if (old == kEmptyKey) return true;
+    }
     if (old == key) return false;
     slot = (slot + 1) & mask;
   }
@@ -78,19 +92,31 @@ __device__ __forceinline__ bool violates(const ProdArgs &A, uint32_t p, uint32_t
 }
 
 // Tests and expands pairs [i0, size) (stride `step`) of frontier `cur` into
-// `nxt`, counting new pairs in *next; sets *bad if a pair violates.
+// `nxt`, counting new pairs in *next; sets *bad if a pair violates.  The lanes
+// of a warp that found new pairs for the same letter take their frontier
+// positions with one atomicAdd (a single counter taking one atomicAdd per new
+// pair serialises the level).
 __device__ __forceinline__ void expand_pairs(const ProdArgs &A, const unsigned long long *cur,
                                              unsigned long long *nxt, uint32_t size, uint32_t i0, uint32_t step,
                                              uint32_t *next, uint32_t *bad) {
+  const uint32_t lane = threadIdx.x & 31u;
   for (uint32_t i = i0; i < size; i += step) {
-    const unsigned long long key = cur[i] - 1;
-    const uint32_t p = (uint32_t)(key / A.nB), q = (uint32_t)(key % A.nB);
+    const uint32_t act = __activemask();
+    const unsigned long long key = cur[i];
+    const uint32_t p = (uint32_t)(key >> 32), q = (uint32_t)key;
     if (violates(A, p, q)) atomicOr(bad, 1u);
     for (uint32_t a = 0; a < A.k; ++a) {
       const uint32_t tp = A.dA[(size_t)a * A.nA + p], tq = A.dB[(size_t)a * A.nB + q];
-      const unsigned long long nk = (unsigned long long)tp * A.nB + tq + 1;
-      if (set_insert(A, nk)) {
-        const uint32_t at = atomicAdd(next, 1u);
+      const unsigned long long nk = ((unsigned long long)tp << 32) | tq;
+      const bool fresh = set_insert(A, nk);
+      const uint32_t m = __ballot_sync(act, fresh);
+      if (m == 0u) continue;
+      const uint32_t first = __ffs(act) - 1;
+      uint32_t base = 0;
+      if (lane == first) base = atomicAdd(next, (uint32_t)__popc(m));
+      base = __shfl_sync(act, base, first);
+      if (fresh) {
+        const uint32_t at = base + __popc(m & ((1u << lane) - 1u));
         if (at < A.cap) nxt[at] = nk;
         else atomicOr(&A.ctrl->err, ERR_TABLE_FULL);
       }
@@ -98,7 +124,7 @@ __device__ __forceinline__ void expand_pairs(const ProdArgs &A, const unsigned l
   }
 }
 
-__global__ void __launch_bounds__(kPThreads) product_kernel(ProdArgs A) {
+__global__ void __launch_bounds__(kPThreads) product_kernel(const __grid_constant__ ProdArgs A) {
   __shared__ uint32_t s_size[2], s_bad;
   Ctrl *C = A.ctrl;
   ProdRing *R = A.ring;
@@ -114,10 +140,10 @@ __global__ void __launch_bounds__(kPThreads) product_kernel(ProdArgs A) {
     if (A.dA[i] >= A.nA) atomicOr(&C->err, ERR_BAD_DELTA);
   for (uint64_t i = tid; i < (uint64_t)A.k * A.nB; i += stride)
     if (A.dB[i] >= A.nB) atomicOr(&C->err, ERR_BAD_DELTA);
-  for (uint64_t i = tid; i < (1ull << A.log2set); i += stride) A.set[i] = 0ull;
+  for (uint64_t i = tid; i < (1ull << A.log2set); i += stride) A.set[i] = kEmptyKey;
   bool ok = grid_sync(C, A.barrier_ns);
   if (ok && leader) {
-    const unsigned long long k0 = (unsigned long long)A.sA * A.nB + A.sB + 1;
+    const unsigned long long k0 = ((unsigned long long)A.sA << 32) | A.sB;
     set_insert(A, k0);
     A.front[0][0] = k0;
     R->size[0] = 1u;   // slot 0: one pair, buffer 0, level 0, no pairs before it
@@ -241,6 +267,16 @@ static ProdLayout prod_layout(const dfa_t *a, const dfa_t *b, uint64_t max_pairs
   return L;
 }
 
+// max_pairs never exceeds n_A n_B, nor kMaxPairs: frontier sizes and positions
+// are 32-bit, and a grid-stride walk over a frontier must not wrap.
+static constexpr uint64_t kMaxPairs = 1ull << 31;
+
+static uint64_t clamp_pairs(const dfa_t *a, const dfa_t *b, uint64_t max_pairs) {
+  const uint64_t all = (uint64_t)a->n * b->n;
+  if (max_pairs > all) max_pairs = all;
+  return max_pairs > kMaxPairs ? kMaxPairs : max_pairs;
+}
+
 }  // namespace dfa
 
 using namespace dfa;
@@ -249,7 +285,7 @@ extern "C" {
 
 size_t dfa_product_workspace_size(const dfa_t *a, const dfa_t *b, uint64_t max_pairs) {
   if (check_dfa(a, "a") != DFA_OK || check_dfa(b, "b") != DFA_OK || a->k != b->k || max_pairs == 0) return 0;
-  if (max_pairs > (uint64_t)a->n * b->n) max_pairs = (uint64_t)a->n * b->n;
+  max_pairs = clamp_pairs(a, b, max_pairs);
   return prod_layout(a, b, max_pairs, a->k > 0 && !is_device_ptr(a->delta), !is_device_ptr(a->accept),
                      b->k > 0 && !is_device_ptr(b->delta), !is_device_ptr(b->accept))
       .total;
@@ -265,7 +301,7 @@ int dfa_product_check(const dfa_t *a, const dfa_t *b, int mode, uint64_t max_pai
   if (max_pairs == 0) return fail(DFA_EINVAL, "max_pairs is 0");
   if (!holds) return fail(DFA_EINVAL, "holds is NULL");
   if (!workspace || !aligned(workspace, 256)) return fail(DFA_EINVAL, "workspace NULL or not 256-byte aligned");
-  if (max_pairs > (uint64_t)a->n * b->n) max_pairs = (uint64_t)a->n * b->n;
+  max_pairs = clamp_pairs(a, b, max_pairs);
   const bool hdA = a->k > 0 && !is_device_ptr(a->delta), haA = !is_device_ptr(a->accept);
   const bool hdB = b->k > 0 && !is_device_ptr(b->delta), haB = !is_device_ptr(b->accept);
   const ProdLayout L = prod_layout(a, b, max_pairs, hdA, haA, hdB, haB);
