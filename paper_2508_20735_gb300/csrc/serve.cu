@@ -952,16 +952,29 @@ static int copy_in_device(dfa_server *s, Req &r, const dfa_t *a, const dfa_t *b)
   return e == cudaSuccess ? DFA_OK : cuda_fail(e, "copy request in");
 }
 
-static int copy_dfa_in(const dfa_t *d, std::vector<uint32_t> &delta, std::vector<uint8_t> &acc) {
+// Copies a request's arrays to host vectors (it waits for arena space) on the
+// server's input stream: a synchronous cudaMemcpy would run on the legacy
+// default stream and wait behind unrelated work.
+static int copy_dfa_in(dfa_server *s, const dfa_t *d, std::vector<uint32_t> &delta, std::vector<uint8_t> &acc) {
   delta.resize((size_t)d->k * d->n);
   acc.resize(d->n);
-  if (d->k > 0) {
-    const cudaError_t e = cudaMemcpy(delta.data(), d->delta, delta.size() * 4, cudaMemcpyDefault);
-    if (e != cudaSuccess) return cuda_fail(e, "copy request delta");
+  cudaError_t e = cudaSuccess;
+  if (d->k > 0) e = cudaMemcpyAsync(delta.data(), d->delta, delta.size() * 4, cudaMemcpyDefault, s->in_stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc.data(), d->accept, d->n, cudaMemcpyDefault, s->in_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->in_stream);
+  return e == cudaSuccess ? DFA_OK : cuda_fail(e, "copy request in");
+}
+
+// One byte of a host or device array: host memory is read directly, device
+// memory through the server's input stream.
+static int read_byte(dfa_server *s, const uint8_t *p, uint8_t *out) {
+  if (!is_device_ptr(p)) {
+    *out = *p;
+    return DFA_OK;
   }
-  const cudaError_t e = cudaMemcpy(acc.data(), d->accept, d->n, cudaMemcpyDefault);
-  if (e != cudaSuccess) return cuda_fail(e, "copy request accept");
-  return DFA_OK;
+  cudaError_t e = cudaMemcpyAsync(out, p, 1, cudaMemcpyDeviceToHost, s->in_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->in_stream);
+  return e == cudaSuccess ? DFA_OK : cuda_fail(e, "read start acceptance");
 }
 
 }  // namespace dfa
@@ -1038,9 +1051,9 @@ int dfa_serve_submit(dfa_server *s, int kind, const dfa_t *a, const dfa_t *b, co
   // states of different acceptance; with early exit no round is needed
   uint8_t acc_a = 0, acc_b = 0;
   if (kind == DFA_REQ_EQUIVALENT) {
-    cudaError_t e = cudaMemcpy(&acc_a, a->accept + a->start, 1, cudaMemcpyDefault);
-    if (e == cudaSuccess) e = cudaMemcpy(&acc_b, b->accept + b->start, 1, cudaMemcpyDefault);
-    if (e != cudaSuccess) return cuda_fail(e, "read start acceptance");
+    const int e = read_byte(s, a->accept + a->start, &acc_a) != DFA_OK ? DFA_ECUDA
+                                                                       : read_byte(s, b->accept + b->start, &acc_b);
+    if (e != DFA_OK) return e;
   }
   const bool sep0 = kind == DFA_REQ_EQUIVALENT && ((acc_a != 0) != (acc_b != 0));
   const bool instant = sep0 && (r->o.flags & DFA_FLAG_EARLY_EXIT);
@@ -1063,10 +1076,10 @@ int dfa_serve_submit(dfa_server *s, int kind, const dfa_t *a, const dfa_t *b, co
         return rc;
       }
     } else {
-      rc = copy_dfa_in(a, r->dA, r->aA);
+      rc = copy_dfa_in(s, a, r->dA, r->aA);
       if (rc != DFA_OK) return rc;
       if (kind == DFA_REQ_EQUIVALENT) {
-        rc = copy_dfa_in(b, r->dB, r->aB);
+        rc = copy_dfa_in(s, b, r->dB, r->aB);
         if (rc != DFA_OK) return rc;
       }
     }
