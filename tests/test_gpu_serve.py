@@ -95,3 +95,81 @@ def test_request_beyond_budget_and_destroy_with_pending(g):
         A = dfagen.random_dfa(20_000, 2, 0.5, i)
         srv.submit_minimise(A.delta, A.accept)
     srv.close()        # cancels what is still queued; must not hang
+
+
+def _as(kind, X):
+    """X's arrays as numpy (pageable host), pinned host tensors or device tensors."""
+    import torch
+    d = np.ascontiguousarray(X.delta)
+    a = np.ascontiguousarray(X.accept)
+    if kind == "numpy":
+        return d, a
+    td, ta = torch.from_numpy(d.view(np.int32)), torch.from_numpy(a)
+    if kind == "pinned":
+        return td.pin_memory(), ta.pin_memory()
+    return td.cuda(), ta.cuda()
+
+
+def test_concurrent_submitters_and_input_kinds(g):
+    """Four client threads submit at once (the C call releases the GIL), with
+    pageable, pinned and device inputs; every verdict and round count equals the
+    stand-alone call's."""
+    import threading
+    pairs = [dfagen.equivalence_pair(i, 23, n_lo=300, n_hi=30_000) for i in range(24)]
+    kinds = ("numpy", "pinned", "device")
+    results = {}
+    with g.Server(1 << 30, max_slots=16) as srv:
+        def client(c):
+            for i in range(c, len(pairs), 4):
+                A, B, _ = pairs[i]
+                ka, kb = kinds[i % 3], kinds[(i + c) % 3]
+                t = srv.submit_equivalent(_as(ka, A) + (A.start,), _as(kb, B) + (B.start,))
+                results[i] = srv.wait(t)
+        threads = [threading.Thread(target=client, args=(c,)) for c in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+    assert sorted(results) == list(range(len(pairs)))
+    for i, (A, B, expect) in enumerate(pairs):
+        st, res, eq, _ = results[i]
+        assert st == g.DFA_OK
+        assert eq == int(expect)
+        alone_eq, alone = g.equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start))
+        assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
+            (alone.num_blocks, alone.rounds_changed, alone.rounds_executed)
+
+
+def test_start_states_apart_with_early_exit(g):
+    """Start states of different acceptance: with early exit the verdict needs
+    no round (the empty word separates them), for host and device inputs."""
+    A = dfagen.random_dfa(1000, 2, 0.5, 3)
+    B_acc = A.accept.copy()
+    B_acc[A.start] ^= 1
+    B = dfagen.DFA(A.delta.copy(), B_acc, A.start)
+    with g.Server(256 << 20, max_slots=4) as srv:
+        for kind in ("numpy", "device"):
+            t = srv.submit_equivalent(_as(kind, A) + (A.start,), _as(kind, B) + (B.start,), early_exit=True)
+            st, res, eq, _ = srv.wait(t)
+            assert st == g.DFA_OK and eq == 0 and res.rounds_executed == 0
+            t = srv.submit_equivalent(_as(kind, A) + (A.start,), _as(kind, B) + (B.start,))
+            st, res, eq, _ = srv.wait(t)
+            assert st == g.DFA_OK and eq == 0
+            assert res.rounds_executed == oracle.equivalent(A.delta, A.accept, A.start, B.delta, B.accept,
+                                                            B.start).refine.rounds_executed
+
+
+def test_bad_targets_fail_alone(g):
+    """A request whose targets are out of range finishes with DFA_EINVAL
+    (validated on the device); requests beside it are unaffected."""
+    good = dfagen.random_dfa(5000, 3, 0.5, 8)
+    bad_delta = good.delta.copy()
+    bad_delta[2][17] = good.n + 5
+    with g.Server(512 << 20, max_slots=8) as srv:
+        t_bad = srv.submit_minimise(bad_delta, good.accept)
+        t_good = srv.submit_minimise(good.delta, good.accept)
+        st, *_ = srv.wait(t_bad)
+        assert st == g.DFA_EINVAL
+        st, res, _, blocks = srv.wait(t_good, n=good.n)
+        assert st == g.DFA_OK
+        assert np.array_equal(blocks, oracle.moore(good.delta, good.accept).block)
