@@ -337,6 +337,7 @@ def extras(g):
         for t in tickets:
             srv.wait(t)
         cap = nreq / (time.perf_counter() - t0)
+        counters = srv.counters()
     rng = np.random.default_rng(5)
     lam = 0.8 * cap
     gaps = rng.exponential(1.0 / lam, nreq)
@@ -366,6 +367,7 @@ def extras(g):
                           "serial_dfa_equivalent_rps": serial, "closed_loop_vs_serial": cap / serial,
                           "offered_rps": lam, "p50_us": s["p50_us"], "p99_us": s["p99_us"],
                           "throughput_rps": s["throughput_rps"], "wrong_verdicts": wrong,
+                          "closed_loop_counters": counters,
                           "sample": "Poisson arrivals at 0.8 x closed-loop capacity; pairs of the served-equivalence "
                                     "recipe (A: n log-uniform in [1e3, 1e6], k in {2, 4}) reused round robin, "
                                     "inputs in pinned host memory"}

@@ -279,6 +279,15 @@ int dfa_serve_wait(dfa_server *s, uint64_t ticket, uint64_t timeout_ns, dfa_resu
 /* Latency percentiles (submit to completion) and throughput of finished requests. */
 int dfa_serve_stats(dfa_server *s, double *p50_us, double *p99_us, double *throughput_rps);
 
+/* Counters since creation: refinement steps run (one round of every admitted
+ * request per step), requests and states advanced by a round (their sums over
+ * the steps), the state sum split by the round's renumbering mode
+ * (mode_state_rounds[3]: direct, filter, table), and host wall time spent in
+ * steps (descriptor upload to results on the host), in microseconds.  Any
+ * pointer may be NULL. */
+int dfa_serve_counters(dfa_server *s, uint64_t *steps, uint64_t *request_rounds, uint64_t *state_rounds,
+                       uint64_t *mode_state_rounds, double *step_us);
+
 /* Cancels outstanding requests, joins the thread and frees the arena.  No other
  * call on `s` may run concurrently with or after this one. */
 int dfa_serve_destroy(dfa_server *s);

@@ -78,6 +78,8 @@ _SIGS = [
     ("dfa_serve_poll", c_int, [c_void_p, c_uint64, POINTER(DfaResult), POINTER(c_int), c_void_p]),
     ("dfa_serve_wait", c_int, [c_void_p, c_uint64, c_uint64, POINTER(DfaResult), POINTER(c_int), c_void_p]),
     ("dfa_serve_stats", c_int, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
+    ("dfa_serve_counters", c_int, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), POINTER(c_uint64),
+                                   POINTER(c_uint64 * 3), POINTER(c_double)]),
     ("dfa_serve_destroy", c_int, [c_void_p]),
     ("dfa_minimise_noalloc", c_int, [POINTER(DfaT), POINTER(DfaOpts), c_void_p, POINTER(DfaResult), c_void_p]),
     ("dfa_product_workspace_size", c_size_t, [POINTER(DfaT), POINTER(DfaT), c_uint64]),
@@ -534,6 +536,19 @@ class Server:
         if st != DFA_OK:
             raise DfaError(st, last_error())
         return {"p50_us": p50.value, "p99_us": p99.value, "throughput_rps": rps.value}
+
+    def counters(self):
+        """Steps run, request-rounds and state-rounds advanced (also by round mode), host time in
+        steps (dfa_serve_counters)."""
+        st_, rr, sr, us = c_uint64(), c_uint64(), c_uint64(), c_double()
+        modes = (c_uint64 * 3)()
+        st = lib().dfa_serve_counters(self._h, ctypes.byref(st_), ctypes.byref(rr), ctypes.byref(sr),
+                                      ctypes.byref(modes), ctypes.byref(us))
+        if st != DFA_OK:
+            raise DfaError(st, last_error())
+        return {"steps": st_.value, "request_rounds": rr.value, "state_rounds": sr.value,
+                "state_rounds_direct": modes[0], "state_rounds_filter": modes[1], "state_rounds_table": modes[2],
+                "step_us": us.value}
 
     def close(self):
         if getattr(self, "_h", None):

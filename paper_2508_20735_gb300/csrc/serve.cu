@@ -644,6 +644,10 @@ struct dfa_server {
   std::chrono::steady_clock::time_point first_submit, last_done;
   bool any_submit = false;
   std::string worker_error;
+  // counters (under mu): steps run, requests and states advanced by one round, host time in steps
+  uint64_t steps = 0, request_rounds = 0, state_rounds = 0;
+  uint64_t mode_state_rounds[3] = {0, 0, 0};   // by round mode: direct, filter, table
+  double step_us = 0.0;
 };
 
 namespace dfa {
@@ -768,6 +772,7 @@ static void worker_main(dfa_server *s) {
     }
     if (act.empty()) continue;
     // ---- one round for every admitted request
+    const auto t_step = std::chrono::steady_clock::now();
     uint32_t ntiles = 0;
     uint32_t max_stages = 1, any_filter = 0;
     uint64_t filter_states = 0;
@@ -850,6 +855,19 @@ static void worker_main(dfa_server *s) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(outs_h, outs, act.size() * sizeof(ServeOut), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ch, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    {
+      uint64_t states = 0, by_mode[3] = {0, 0, 0};
+      for (auto &r : act) {
+        states += r->n;
+        by_mode[r->mode == SM_DIRECT ? 0 : r->mode == SM_FILTER ? 1 : 2] += r->n;
+      }
+      std::lock_guard<std::mutex> lock(s->mu);
+      for (int m = 0; m < 3; ++m) s->mode_state_rounds[m] += by_mode[m];
+      s->steps += 1;
+      s->request_rounds += act.size();
+      s->state_rounds += states;
+      s->step_us += std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t_step).count();
+    }
     if (e != cudaSuccess || ch.err) {
       std::lock_guard<std::mutex> lock(s->mu);
       s->worker_error = e != cudaSuccess ? cudaGetErrorString(e) : "device-side error in a serving step";
@@ -1168,6 +1186,19 @@ int dfa_serve_stats(dfa_server *s, double *p50_us, double *p99_us, double *throu
   if (p99_us) *p99_us = pct(0.99);
   const double span = std::chrono::duration<double>(s->last_done - s->first_submit).count();
   if (throughput_rps) *throughput_rps = span > 0 ? v.size() / span : 0;
+  return DFA_OK;
+}
+
+int dfa_serve_counters(dfa_server *s, uint64_t *steps, uint64_t *request_rounds, uint64_t *state_rounds,
+                       uint64_t *mode_state_rounds, double *step_us) {
+  if (!s) return fail(DFA_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (steps) *steps = s->steps;
+  if (request_rounds) *request_rounds = s->request_rounds;
+  if (state_rounds) *state_rounds = s->state_rounds;
+  if (mode_state_rounds)
+    for (int m = 0; m < 3; ++m) mode_state_rounds[m] = s->mode_state_rounds[m];
+  if (step_us) *step_us = s->step_us;
   return DFA_OK;
 }
 

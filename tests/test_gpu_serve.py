@@ -72,6 +72,9 @@ def test_mix_equals_alone(g, slots, budget_mb):
                     (alone.num_blocks, alone.rounds_changed, alone.rounds_executed)
         s = srv.stats()
         assert s["p50_us"] > 0 and s["p99_us"] >= s["p50_us"] and s["throughput_rps"] > 0
+        c = srv.counters()
+        assert c["steps"] > 0 and c["request_rounds"] >= len(reqs) and c["step_us"] > 0
+        assert c["state_rounds"] == c["state_rounds_direct"] + c["state_rounds_filter"] + c["state_rounds_table"]
 
 
 def test_poll_busy_then_done(g):
