@@ -48,9 +48,12 @@ def parse():
                     help="profiling cases: 2^lg states instead of 2^24 (same k, seed and acceptance)")
     ap.add_argument("--stop-discrete", action="store_true",
                     help="profiling cases: time the call with DFA_FLAG_STOP_DISCRETE")
-    ap.add_argument("--case", default="headline", choices=["headline", "batch"],
+    ap.add_argument("--case", default="headline", choices=["headline", "batch", "serve"],
                     help="batch: time only the packed batched call on --batch-dfas DFAs of the batch recipe")
     ap.add_argument("--batch-dfas", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     ap.add_argument("--schedule", type=int, default=-1, help="batch case: kernel schedule (-1 = autotuned)")
     args = ap.parse_args()
     if args.lg != 24:
@@ -405,11 +408,57 @@ def run_batch_case(args, local):
                       "clocks": clk.summary(), "gpu_launches": args.steps}), flush=True)
 
 
+def run_serve_case(args, local):
+    """The served-equivalence workload alone: each step submits --serve-requests
+    requests (pairs of the served-equivalence recipe, seed 5, drawn round robin
+    from 24 generated pairs whose arrays sit in pinned host memory) to one server
+    and waits for all of them (closed loop)."""
+    import numpy as np
+    import torch
+
+    import dfagen
+    import paper_2508_20735_gb300 as g
+    torch.cuda.set_device(local)
+    g.build()
+
+    def _pinned(X):
+        return (torch.from_numpy(np.ascontiguousarray(X.delta).view(np.int32)).pin_memory(),
+                torch.from_numpy(np.ascontiguousarray(X.accept)).pin_memory(), X.start)
+    pool = [(_pinned(A), _pinned(B)) for A, B, _ in (dfagen.equivalence_pair(i, 5) for i in range(24))]
+    nreq = args.serve_requests
+    with g.Server(int(args.serve_budget_gb * (1 << 30)), max_slots=args.serve_slots) as srv:
+        def step():
+            tickets = [srv.submit_equivalent(*pool[i % len(pool)]) for i in range(nreq)]
+            for t in tickets:
+                srv.wait(t)
+        for _ in range(args.warmup):
+            step()
+        c0 = srv.counters()
+        with ClockSampler(local) as clk:
+            t = time.perf_counter()
+            for _ in range(args.steps):
+                step()
+            el = time.perf_counter() - t
+        c1 = srv.counters()
+    d = {k: c1[k] - c0[k] for k in c1}
+    print(json.dumps({"metric": "equivalence requests/sec (served, closed loop)", "value": nreq * args.steps / el,
+                      "unit": "requests/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "dtype": "u32",
+                      "data": "synthetic", "config": {"workload": f"serve_equiv_{nreq}_requests",
+                                                      "max_slots": args.serve_slots,
+                                                      "hbm_budget_gb": args.serve_budget_gb},
+                      "counters": d, "clocks": clk.summary(), "gpu_launches": int(d["steps"])}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.case == "serve":
+        if rank == 0:
+            run_serve_case(args, local)
         return
     if args.case == "batch":
         if rank == 0:
