@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--case", default="headline", choices=["headline", "batch", "serve"],
                     help="batch: time only the packed batched call on --batch-dfas DFAs of the batch recipe")
     ap.add_argument("--batch-dfas", type=int, default=4096)
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=10_000)
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     ap.add_argument("--schedule", type=int, default=-1, help="batch case: kernel schedule (-1 = autotuned)")
@@ -333,7 +333,7 @@ def extras(g):
         return (torch.from_numpy(np.ascontiguousarray(X.delta).view(np.int32)).pin_memory(),
                 torch.from_numpy(np.ascontiguousarray(X.accept)).pin_memory(), X.start)
     pool = [(_pinned(A), _pinned(B), eq) for A, B, eq in (dfagen.equivalence_pair(i, 5) for i in range(24))]
-    nreq = 400
+    nreq = 10_000
     with g.Server(24 << 30, max_slots=64) as srv:
         t0 = time.perf_counter()
         tickets = [srv.submit_equivalent(A, B) for A, B, _ in (pool[i % len(pool)] for i in range(nreq))]

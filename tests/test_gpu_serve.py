@@ -176,3 +176,26 @@ def test_bad_targets_fail_alone(g):
         st, res, _, blocks = srv.wait(t_good, n=good.n)
         assert st == g.DFA_OK
         assert np.array_equal(blocks, oracle.moore(good.delta, good.accept).block)
+
+
+def test_served_equivalence_recipe_full_sizes(g):
+    """The served-equivalence workload at its full sizes (A: n log-uniform in
+    [1e3, 1e6], k in {2, 4}; B a renamed copy plus junk, half with a reachable
+    accepting bit flipped): 2,000 Poisson-free requests cycling through 32
+    generated pairs; every verdict is the generator's and every round count
+    equals the stand-alone dfa_equivalent call's."""
+    import torch
+    pairs = [dfagen.equivalence_pair(i, 5) for i in range(32)]
+    dev = [((torch.from_numpy(A.delta.view(np.int32)).cuda(), torch.from_numpy(A.accept).cuda(), A.start),
+            (torch.from_numpy(B.delta.view(np.int32)).cuda(), torch.from_numpy(B.accept).cuda(), B.start), eq)
+           for A, B, eq in pairs]
+    alone = [g.equivalent(a, b)[1] for a, b, _ in dev]
+    with g.Server(24 << 30, max_slots=64) as srv:
+        tickets = [srv.submit_equivalent(dev[i % 32][0], dev[i % 32][1]) for i in range(2000)]
+        for i, t in enumerate(tickets):
+            st, res, eq, _ = srv.wait(t)
+            assert st == g.DFA_OK
+            assert eq == int(dev[i % 32][2])
+            ref = alone[i % 32]
+            assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
+                (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
