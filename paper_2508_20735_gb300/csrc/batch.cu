@@ -117,12 +117,21 @@ enum : uint32_t { BM_DIRECT = 0, BM_FILTER = 1, BM_TABLE = 2 };
 
 // Mode of a DFA's round r (w = its words in the bookkeeping array, as they
 // stand before the round): direct when the packed signature fits in log2S
-// bits; filter when the previous round left at least n/64 blocks (most blocks
-// small); otherwise table.
+// bits; filter when most signatures are likely unique: the previous round left
+// at least n/64 blocks (most blocks small), or its B blocks allow B^(k+1) >= 64 n
+// combinations (many letters: a signature then rarely repeats even while the
+// blocks are large); otherwise table.  Filter rounds are exact either way; a
+// filter round that lists most states hands the DFA's later rounds to the table.
 __device__ __forceinline__ uint32_t batch_mode(const SegInfo &S, const uint32_t *w, uint32_t r) {
   const uint32_t wd = w[SS_W];
   if ((uint64_t)(S.k + 1) * wd <= S.log2S) return BM_DIRECT;
-  if (r > 1 && w[SS_FOK] && (uint64_t)w[SS_PREV] * 64 >= S.n) return BM_FILTER;
+  if (r > 1 && w[SS_FOK]) {
+    const uint32_t prev = w[SS_PREV];
+    if ((uint64_t)prev * 64 >= S.n) return BM_FILTER;
+    const uint32_t lg_prev = prev > 1 ? 31u - __clz(prev) : 0u;            // floor(log2 B)
+    const uint32_t lg_n = 32u - __clz(S.n - 1u | 1u);                       // ceil(log2 n)
+    if ((uint64_t)(S.k + 1) * lg_prev >= (uint64_t)lg_n + 6) return BM_FILTER;
+  }
   return BM_TABLE;
 }
 
