@@ -127,10 +127,7 @@ __device__ __forceinline__ uint32_t batch_mode(const SegInfo &S, const uint32_t 
   if ((uint64_t)(S.k + 1) * wd <= S.log2S) return BM_DIRECT;
   if (r > 1 && w[SS_FOK]) {
     const uint32_t prev = w[SS_PREV];
-    if ((uint64_t)prev * 64 >= S.n) return BM_FILTER;
-    const uint32_t lg_prev = prev > 1 ? 31u - __clz(prev) : 0u;            // floor(log2 B)
-    const uint32_t lg_n = 32u - __clz(S.n - 1u | 1u);                       // ceil(log2 n)
-    if ((uint64_t)(S.k + 1) * lg_prev >= (uint64_t)lg_n + 6) return BM_FILTER;
+    if ((uint64_t)prev * 64 >= S.n || signatures_sparse(S.k, prev, S.n)) return BM_FILTER;
   }
   return BM_TABLE;
 }

@@ -48,6 +48,16 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
+// B^(k+1) >= 64 n: the previous round's B blocks allow far more signatures
+// than there are states, so a signature rarely repeats even while the blocks
+// are large (a DFA with many letters, early rounds).  Filter rounds suit that.
+__host__ __device__ __forceinline__ bool signatures_sparse(uint32_t k, uint32_t B, uint32_t n) {
+  uint32_t lg_b = 0, lg_n = 0;                                          // floor(log2 B), ceil(log2 n)
+  while (lg_b < 31u && (B >> (lg_b + 1u)) != 0u) ++lg_b;
+  while (lg_n < 32u && ((uint64_t)1 << lg_n) < n) ++lg_n;
+  return (uint64_t)(k + 1u) * lg_b >= (uint64_t)lg_n + 6u;
+}
+
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

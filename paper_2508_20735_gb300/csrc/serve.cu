@@ -781,7 +781,10 @@ static void worker_main(dfa_server *s) {
       r.round += 1;
       // the round's mode, as dfa_minimise chooses it
       if ((uint64_t)(r.k + 1) * r.w <= r.log2S) r.mode = SM_DIRECT;
-      else if (r.round > 1 && r.fok && (uint64_t)r.prevB * 64 >= r.n) r.mode = SM_FILTER;
+      else if (r.round > 1 && r.fok &&
+               ((uint64_t)r.prevB * 64 >= r.n ||
+                (r.kind == DFA_REQ_MINIMISE && signatures_sparse(r.k, r.prevB, r.n))))
+        r.mode = SM_FILTER;   // most signatures unique (a union's states come in pairs: not predicted)
       else r.mode = SM_TABLE;
       const StagePlan P = make_plan(r.k, r.w, r.log2S);
       const uint32_t stages = r.mode == SM_DIRECT ? 0u : P.stages;
