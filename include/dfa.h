@@ -198,6 +198,22 @@ size_t dfa_equivalent_workspace_size(const dfa_t *a, const dfa_t *b, const dfa_o
 int dfa_equivalent(const dfa_t *a, const dfa_t *b, const dfa_opts *opts, int *equivalent,
                    dfa_result *res, void *workspace, size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------- stream-ordered minimisation */
+
+/* dfa_minimise (signature refinement, DFA_ALGO_MOORE only) enqueued on `stream`
+ * without waiting: the staging of host inputs, the refinement and the copy of
+ * block_out (host or device) are stream-ordered, so several calls on different
+ * streams overlap one call's copies with another's refinement.  The arrays and
+ * the workspace must stay valid, and untouched by other work, until
+ * dfa_minimise_result has returned.  Argument errors are returned at once;
+ * errors found on the device (a target >= n, a timeout) by dfa_minimise_result. */
+int dfa_minimise_async(const dfa_t *d, const dfa_opts *opts, uint32_t *block_out, void *workspace, size_t ws_bytes,
+                       void *stream);
+
+/* Waits for `stream` and returns the status of the dfa_minimise_async call that
+ * used `workspace` on it; fills *res (host, may be NULL) as dfa_minimise does. */
+int dfa_minimise_result(const void *workspace, dfa_result *res, void *stream);
+
 /* ---------------------------------------------------------------- product exploration */
 
 #define DFA_CHECK_EQUIVALENCE 0   /* L(A) = L(B) */

@@ -88,6 +88,8 @@ _SIGS = [
     ("dfa_quotient_workspace_size", c_size_t, [POINTER(DfaT), c_void_p, c_void_p, c_void_p]),
     ("dfa_quotient", c_int, [POINTER(DfaT), c_void_p, c_void_p, c_void_p, POINTER(c_uint32), POINTER(c_uint32),
                              c_void_p, c_size_t, c_void_p]),
+    ("dfa_minimise_async", c_int, [POINTER(DfaT), POINTER(DfaOpts), c_void_p, c_void_p, c_size_t, c_void_p]),
+    ("dfa_minimise_result", c_int, [c_void_p, POINTER(DfaResult), c_void_p]),
     ("dfa_trans_workspace_size", c_size_t, [POINTER(DfaT), c_void_p]),
     ("dfa_trans", c_int, [POINTER(DfaT), c_void_p, POINTER(c_uint32), c_void_p, c_size_t, c_void_p]),
     ("dfa_probe_l2_gather", c_int, [c_void_p, c_size_t, c_uint64, c_void_p, POINTER(c_double)]),
@@ -433,6 +435,20 @@ def quotient(delta, accept, start, block, workspace=None, stream=None):
         raise DfaError(st, last_error())
     m = nq.value
     return dout[:k * m].reshape(k, m), aout[:m], sq.value
+
+
+def minimise_async(d: DfaT, opts: DfaOpts | None, block_out_ptr: int, workspace_ptr: int, ws_bytes: int,
+                   stream: int) -> int:
+    """dfa_minimise_async on an already built dfa_t (see make_dfa): enqueue only."""
+    return int(lib().dfa_minimise_async(ctypes.byref(d), ctypes.byref(opts) if opts else None, block_out_ptr,
+                                        workspace_ptr, int(ws_bytes), stream))
+
+
+def minimise_result(workspace_ptr: int, stream: int) -> tuple[int, DfaResult]:
+    """dfa_minimise_result: wait for the stream; (status, DfaResult)."""
+    res = DfaResult()
+    st = lib().dfa_minimise_result(workspace_ptr, ctypes.byref(res), stream)
+    return int(st), res
 
 
 DFA_TRANS_MAX_STATES = 256

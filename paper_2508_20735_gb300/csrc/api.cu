@@ -133,9 +133,9 @@ MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_ac
 
 // Runs the Moore kernel over a device-resident DFA (delta/accept are device
 // pointers) writing canonical blocks to out_dev.  Fills *ctrl_host.
-int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
-              const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
-              Ctrl *ctrl_host, uint32_t vec_ok) {
+int enqueue_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
+                  const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
+                  uint32_t vec_ok) {
   MooreArgs a{};
   a.delta = delta_dev;
   a.accept = accept_dev;
@@ -186,7 +186,15 @@ int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, 
   if ((size_t)li.grid > kMaxGrid) return fail(DFA_ECUDA, "grid of %d blocks exceeds %zu", li.grid, kMaxGrid);
   e = launch_moore(a, st, &li);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the refinement kernel");
-  e = cudaMemcpyAsync(ctrl_host, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+  return DFA_OK;
+}
+
+int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
+              const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
+              Ctrl *ctrl_host, uint32_t vec_ok) {
+  const int rc = enqueue_moore(delta_dev, accept_dev, n, k, out_dev, L, ws, o, st, track, vec_ok);
+  if (rc != DFA_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(ctrl_host, ws + L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(ctrl)");
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "refinement kernel");

@@ -35,6 +35,10 @@ MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_ac
 int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
               const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
               Ctrl *ctrl_host, uint32_t vec_ok);
+// the refinement kernel's launch alone (no wait): control block at ws + L.ctrl
+int enqueue_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
+                  const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
+                  uint32_t vec_ok);
 int status_from_ctrl(const Ctrl &c);
 
 // naivePR / transPR (naive.cu)

@@ -284,3 +284,70 @@ def test_equivalence_self(g):
     A = dfagen.random_dfa(12_345, 2, 0.5, 8)
     eq, _ = g.equivalent((A.delta, A.accept, 3), (A.delta, A.accept, 3))
     assert eq
+
+
+# ---------------------------------------------------------------- stream-ordered calls
+
+def test_async_pipeline_equals_oracle(g):
+    """dfa_minimise_async on two streams with two workspaces, each call issued
+    before the previous one on the other stream has finished, host and device
+    buffers alternating: every partition and round count equals the oracle's."""
+    import torch
+    dfas = [dfagen.random_dfa(n, k, 0.5, s) for n, k, s in ((10_000, 2, 1), (300_000, 4, 2), (4097, 3, 3),
+                                                             (65_536, 8, 4), (1, 2, 5), (200_000, 2, 6))]
+    dfas.append(dfagen.planted_redundancy(dfagen.random_dfa(3000, 3, 0.5, 7), 5, 2)[0])
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    opts = g.make_opts("moore")
+    nmax, kmax = max(A.n for A in dfas), max(A.k for A in dfas)
+    probe, _ = g.make_dfa(np.zeros((kmax, nmax), np.uint32), np.zeros(nmax, np.uint8))
+    wsb = g.dfa_workspace_size(probe, opts)
+    ws = [g._workspace(wsb), g._workspace(wsb)]
+    keep, pending = [], {}
+    for i, A in enumerate(dfas):
+        s = i % 2
+        if s in pending:
+            j = pending.pop(s)
+            _check_async(g, dfas[j], keep[j], ws[s], streams[s])
+        if i % 4 < 2:   # host buffers (pinned)
+            arrs = (torch.from_numpy(np.ascontiguousarray(A.delta).view(np.int32)).pin_memory(),
+                    torch.from_numpy(np.ascontiguousarray(A.accept)).pin_memory())
+            out = torch.empty(A.n, dtype=torch.int32).pin_memory()
+        else:
+            arrs = (torch.from_numpy(np.ascontiguousarray(A.delta).view(np.int32)).cuda(),
+                    torch.from_numpy(np.ascontiguousarray(A.accept)).cuda())
+            out = torch.empty(A.n, dtype=torch.int32, device="cuda")
+        d, k2 = g.make_dfa(arrs[0], arrs[1])
+        keep.append((d, k2, arrs, out))
+        assert g.minimise_async(d, opts, out.data_ptr(), ws[s].data_ptr(), wsb, streams[s].cuda_stream) == g.DFA_OK
+        pending[s] = i
+    for s, j in pending.items():
+        _check_async(g, dfas[j], keep[j], ws[s], streams[s])
+
+
+def _check_async(g, A, kept, ws, stream):
+    st, res = g.minimise_result(ws.data_ptr(), stream.cuda_stream)
+    assert st == g.DFA_OK, g.last_error()
+    out = kept[3]
+    got = out.cpu().numpy().view(np.uint32) if out.is_cuda else out.numpy().view(np.uint32)
+    ref = oracle.moore(A.delta, A.accept)
+    assert np.array_equal(got, ref.block)
+    assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
+        (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
+
+
+def test_async_reports_device_errors(g):
+    import torch
+    A = dfagen.random_dfa(1000, 2, 0.5, 5)
+    bad = A.delta.copy()
+    bad[0][3] = 5000
+    d, keep = g.make_dfa(bad, A.accept)
+    opts = g.make_opts("moore")
+    wsb = g.dfa_workspace_size(d, opts)
+    ws = g._workspace(wsb)
+    out = np.empty(A.n, dtype=np.uint32)
+    s = torch.cuda.Stream()
+    assert g.minimise_async(d, opts, out.ctypes.data, ws.data_ptr(), wsb, s.cuda_stream) == g.DFA_OK
+    st, _ = g.minimise_result(ws.data_ptr(), s.cuda_stream)
+    assert st == g.DFA_EINVAL
+    opts_naive = g.make_opts("naive")
+    assert g.minimise_async(d, opts_naive, out.ctypes.data, ws.data_ptr(), wsb, s.cuda_stream) == g.DFA_EINVAL
