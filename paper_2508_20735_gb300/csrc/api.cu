@@ -135,7 +135,7 @@ MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_ac
 // pointers) writing canonical blocks to out_dev.  Fills *ctrl_host.
 int enqueue_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
                   const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
-                  uint32_t vec_ok) {
+                  uint32_t vec_ok, bool independent_letters) {
   MooreArgs a{};
   a.delta = delta_dev;
   a.accept = accept_dev;
@@ -172,6 +172,11 @@ int enqueue_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t
   a.barrier_ns = o.timeout_ns < 5000000000ull ? o.timeout_ns : 5000000000ull;
   a.vec = vec_ok;
   a.stream_delta = ((uint64_t)k * n * 4 > (64ull << 20)) ? 1u : 0u;
+  // filter rounds from the sparse-signature estimate: only for a DFA's own letters (closure letters
+  // are powers of one letter, far from independent), not for a union (its states come in pairs),
+  // and only from 2^20 states on (below, a filter round's extra grid barriers cost more than the
+  // table round's random inserts: 117 against 101 us at 10,000 states)
+  a.predict_sparse = (independent_letters && !track && n >= (1u << 20)) ? 1u : 0u;
   if (track) {
     a.track_pair = 1;
     a.sep_a = track->a;
@@ -191,8 +196,8 @@ int enqueue_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t
 
 int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
               const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
-              Ctrl *ctrl_host, uint32_t vec_ok) {
-  const int rc = enqueue_moore(delta_dev, accept_dev, n, k, out_dev, L, ws, o, st, track, vec_ok);
+              Ctrl *ctrl_host, uint32_t vec_ok, bool independent_letters) {
+  const int rc = enqueue_moore(delta_dev, accept_dev, n, k, out_dev, L, ws, o, st, track, vec_ok, independent_letters);
   if (rc != DFA_OK) return rc;
   cudaError_t e = cudaMemcpyAsync(ctrl_host, ws + L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(ctrl)");
@@ -278,7 +283,7 @@ static int run_closure_moore(const dfa_t *d, const dfa_opts &o, uint32_t *block_
   const uint32_t rows = d->k * (C.L + 1);
   uint32_t *out = ho ? reinterpret_cast<uint32_t *>(wm + C.m.out) : block_out;
   Ctrl c{};
-  rc = run_moore(dT, accept, d->n, rows, out, C.m, wm, o, st, nullptr, &c, 1u);
+  rc = run_moore(dT, accept, d->n, rows, out, C.m, wm, o, st, nullptr, &c, 1u, false);
   if (rc != DFA_OK) return rc;
   const int status = status_from_ctrl(c);
   if (res) {

@@ -32,13 +32,15 @@ int check_dfa(const dfa_t *d, const char *name);
 bool aligned(const void *p, size_t a);
 uint32_t pick_vec(uint32_t n, uint32_t k, const void *delta, const void *accept, int32_t schedule);
 MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_accept, bool stage_out);
+// independent_letters: the letters are the DFA's own (not closure letters, which are
+// powers of the same letter), so the sparse-signature estimate may pick filter rounds
 int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
               const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
-              Ctrl *ctrl_host, uint32_t vec_ok);
+              Ctrl *ctrl_host, uint32_t vec_ok, bool independent_letters = true);
 // the refinement kernel's launch alone (no wait): control block at ws + L.ctrl
 int enqueue_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,
                   const MooreLayout &L, char *ws, const dfa_opts &o, cudaStream_t st, const PairTrack *track,
-                  uint32_t vec_ok);
+                  uint32_t vec_ok, bool independent_letters = true);
 int status_from_ctrl(const Ctrl &c);
 
 // naivePR / transPR (naive.cu)

@@ -52,9 +52,14 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // than there are states, so a signature rarely repeats even while the blocks
 // are large (a DFA with many letters, early rounds).  Filter rounds suit that.
 __host__ __device__ __forceinline__ bool signatures_sparse(uint32_t k, uint32_t B, uint32_t n) {
-  uint32_t lg_b = 0, lg_n = 0;                                          // floor(log2 B), ceil(log2 n)
+#ifdef __CUDA_ARCH__
+  const uint32_t lg_b = B > 1u ? 31u - (uint32_t)__clz(B) : 0u;        // floor(log2 B)
+  const uint32_t lg_n = n > 1u ? 32u - (uint32_t)__clz(n - 1u) : 0u;   // ceil(log2 n)
+#else
+  uint32_t lg_b = 0, lg_n = 0;
   while (lg_b < 31u && (B >> (lg_b + 1u)) != 0u) ++lg_b;
   while (lg_n < 32u && ((uint64_t)1 << lg_n) < n) ++lg_n;
+#endif
   return (uint64_t)(k + 1u) * lg_b >= (uint64_t)lg_n + 6u;
 }
 

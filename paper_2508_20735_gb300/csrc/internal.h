@@ -78,6 +78,7 @@ struct MooreArgs {
   unsigned long long barrier_ns;  // limit on one barrier wait
   uint32_t vec;            // states per lane in table rounds: 1, 2 or 4
   uint32_t modes;          // bit 0: allow direct rounds, bit 1: allow filter rounds
+  uint32_t predict_sparse; // 1: filter rounds also when B^(k+1) >= 64 n predicts unique signatures
   uint32_t stream_delta;   // 1: load δ with evict-first hints (table larger than L2)
   // equivalence by union: stop when these two states separate (if early_exit)
   uint32_t sep_a, sep_b;

@@ -553,8 +553,8 @@ __global__ void __launch_bounds__(kThreads, 2) moore_kernel(MooreArgs A) {
     uint32_t mode = MODE_TABLE;
     if ((A.modes & 1u) && K <= A.log2S && K <= 27) mode = MODE_DIRECT;
     else if ((A.modes & 2u) && filter_ok && !round1 &&
-             ((uint64_t)B_prev * 64 >= A.n || (!A.track_pair && signatures_sparse(A.k, B_prev, A.n))))
-      mode = MODE_FILTER;   // most signatures unique (a union's states come in pairs: not predicted)
+             ((uint64_t)B_prev * 64 >= A.n || (A.predict_sparse && signatures_sparse(A.k, B_prev, A.n))))
+      mode = MODE_FILTER;   // most signatures unique
     if (mode == MODE_TABLE && !table_clean) {   // first table round: the table starts clean
       clear_table(A.table, A.log2S);
       ok = grid_sync(C, A.barrier_ns);

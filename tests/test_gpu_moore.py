@@ -351,3 +351,12 @@ def test_async_reports_device_errors(g):
     assert st == g.DFA_EINVAL
     opts_naive = g.make_opts("naive")
     assert g.minimise_async(d, opts_naive, out.ctypes.data, ws.data_ptr(), wsb, s.cuda_stream) == g.DFA_EINVAL
+
+
+def test_many_letters_large_against_oracle(g):
+    """From 2^20 states on, a DFA with many letters takes filter rounds while the
+    previous round's blocks are still few (B^(k+1) >= 64 n): the partition and
+    rounds still equal the oracle's."""
+    A = dfagen.random_dfa((1 << 20) + 3, 8, 0.5, 21)
+    _assert_parity(g, A, ref=oracle.moore(A.delta, A.accept))
+
