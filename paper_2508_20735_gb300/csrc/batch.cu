@@ -1025,15 +1025,25 @@ static void tune_save() {
   fclose(f);
 }
 
+// The device's name, looked up once per device (a full property query per
+// batched call would add host time to every call).
+static std::string device_name(int dev) {
+  static std::mutex mu;
+  static std::map<int, std::string> names;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = names.find(dev);
+  if (it != names.end()) return it->second;
+  cudaDeviceProp prop;
+  std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? std::string(prop.name) : "unknown";
+  names[dev] = name;
+  return name;
+}
+
 static std::string tune_key(uint64_t states, uint32_t count, uint32_t kmax) {
   int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceProp prop;
-  cudaGetDeviceProperties(&prop, dev);
-  char buf[256];
-  snprintf(buf, sizeof buf, "batch|%s|states2^%u|dfas2^%u|kmax%u", prop.name, ceil_log2(states + 1),
-           ceil_log2((uint64_t)count + 1), kmax);
-  return buf;
+  return "batch|" + device_name(dev) + "|states2^" + std::to_string(ceil_log2(states + 1)) + "|dfas2^" +
+         std::to_string(ceil_log2((uint64_t)count + 1)) + "|kmax" + std::to_string(kmax);
 }
 
 }  // namespace dfa
