@@ -574,12 +574,12 @@ def main():
     l2 = None
     try:
         probe = torch.zeros(1 << 24, dtype=torch.int32, device="cuda")
-        peak_l2 = g.probe_l2_gather(probe, 1 << 28, stream=stream)
+        peak_l2 = l2probe_gather(probe, 1 << 28, stream=stream)
         del probe
         req = (k + 1) * n * statistics.mean(rounds)
         l2 = {"bound": "l2_random_requests", "achieved": req / kernel_s / 1e9, "peak": peak_l2 / 1e9,
               "unit": "G requests/s", "frac": req / kernel_s / peak_l2,
-              "requests_per_launch": req, "peak_source": "dfa_probe_l2_gather, measured in this run (64 MiB array)"}
+              "requests_per_launch": req, "peak_source": "bench_l2probe.cu, measured in this run (64 MiB array)"}
     except Exception as exc:   # a measurement aid: report why it is missing
         l2 = {"unavailable": str(exc)}
 
@@ -655,6 +655,45 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- the L2 probe (a measurement aid)
+L2PROBE_SRC = os.path.join(ROOT, "bench_l2probe.cu")
+L2PROBE_LIB = os.path.join(ROOT, "_build", "libl2probe.so")
+
+
+def build_l2probe() -> str:
+    """Compiles bench_l2probe.cu (sm_103a) into _build/libl2probe.so when stale.
+    The probe is kept out of the product library: it measures the GPU, not the method."""
+    import shutil
+    if os.path.exists(L2PROBE_LIB) and os.path.getmtime(L2PROBE_LIB) >= os.path.getmtime(L2PROBE_SRC):
+        return L2PROBE_LIB
+    os.makedirs(os.path.dirname(L2PROBE_LIB), exist_ok=True)
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    tmp = L2PROBE_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+                        "-Xcompiler", "-fPIC", "-shared", L2PROBE_SRC, "-o", tmp], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on bench_l2probe.cu:\n{r.stderr}")
+    os.replace(tmp, L2PROBE_LIB)
+    return L2PROBE_LIB
+
+
+def l2probe_gather(table, reads: int = 1 << 28, stream=None) -> float:
+    """Random 4-byte reads per second from `table` (a CUDA tensor whose byte size
+    is a power of two; 64 MiB stays in L2)."""
+    import ctypes
+    lib = ctypes.CDLL(build_l2probe())
+    lib.l2probe_gather.restype = ctypes.c_int
+    lib.l2probe_gather.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_double)]
+    lib.l2probe_error.restype = ctypes.c_char_p
+    rate = ctypes.c_double(0.0)
+    st = lib.l2probe_gather(table.data_ptr(), table.numel() * table.element_size(), int(reads),
+                            stream.cuda_stream if stream is not None else None, ctypes.byref(rate))
+    if st != 0:
+        raise ValueError(f"l2probe_gather: {lib.l2probe_error().decode()} ({st})")
+    return rate.value
 
 
 # the sources the signature-refinement kernel and its launch are compiled from

@@ -98,6 +98,19 @@ typedef enum dfa_algo {
                                       dfa_equivalent; ignored by naivePR, transPR and the
                                       server. */
 
+#define DFA_FLAG_BUCKETED 0x8u   /* signature refinement: read each round's labels through the bucketed
+                                      gather (1 <= k <= 16, at most 2^26 states).  Once per call the
+                                      transitions are sorted by (source range, target range); every
+                                      round then streams them, reads the labels of one target range
+                                      at a time from shared memory, and rebuilds each source range's
+                                      signatures in shared memory, instead of k random label reads
+                                      per state.  Same results; more workspace (dfa_workspace_size
+                                      accounts for it).  Off by default: the direct reads measured
+                                      faster on GB300.  Honoured by dfa_minimise,
+                                      dfa_minimise_async and dfa_equivalent. */
+#define DFA_FLAG_GATHER 0x10u    /* signature refinement: never use the bucketed gather, even with
+                                      DFA_FLAG_BUCKETED set; same results */
+
 typedef struct dfa_opts {
   int32_t algo;            /* dfa_algo */
   uint32_t max_rounds;     /* 0 = no limit; otherwise DFA_EMAXROUNDS after this many rounds */
@@ -318,8 +331,10 @@ int dfa_serve_destroy(dfa_server *s);
  * the library, held by every GPU that loads it until the process exits.
  *  - n <= DFA_NOALLOC_MAX_STATES, else DFA_EINVAL (use dfa_minimise).
  *  - delta, accept and block_out must be device pointers (else DFA_EINVAL).
- *  - The first call on a device looks the array's device address up; make
- *    that first call before any stream capture.
+ *  - The first call on a device looks the array's device address up.
+ *  - Synchronous: the call waits for `stream` before it returns (it reads the
+ *    round counts back), so it must not be called while `stream` is being
+ *    captured into a CUDA graph.
  *  - All calls share the array: calls that overlap on the GPU race, so
  *    serialise them.  Each call clears what it needs; nothing carries over.
  *  - Calls no cudaMalloc, cudaFree or allocating library routine. */
@@ -330,20 +345,6 @@ int dfa_minimise_noalloc(const dfa_t *dfa, const dfa_opts *opts, uint32_t *block
 /* ---------------------------------------------------------------- misc */
 
 /* Thread-local message describing the last failing call on this thread. */
-/* ---------------------------------------------------------------- measurement aid */
-
-/* Rate of random 4-byte reads from an array small enough to stay in L2: the
- * ceiling of the label gathers of every refinement round (k n reads with no
- * pattern per round, one L2 request each).  No counterpart in the paper.
- *   table        device memory of table_bytes (a power of two >= 8; 64 MiB
- *                matches the 2^24-state label array); read only, caller-owned;
- *   reads        reads to time (rounded up to a whole number per thread);
- *   stream       stream to run on (NULL = legacy default stream);
- *   reads_per_s  out: reads per second of the timed pass (one untimed pass
- *                first brings the table into L2).
- * Synchronises the stream.  DFA_EINVAL for a bad size or a host pointer. */
-int dfa_probe_l2_gather(void *table, size_t table_bytes, uint64_t reads, void *stream, double *reads_per_s);
-
 const char *dfa_last_error(void);
 
 /* Library version string. */

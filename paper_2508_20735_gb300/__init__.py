@@ -27,6 +27,8 @@ ALGOS = {"moore": 0, "naive": 1, "trans": 2, "closure_moore": 3, "sort": 4}
 DFA_FLAG_EARLY_EXIT = 0x1
 DFA_FLAG_TABLE_ONLY = 0x2
 DFA_FLAG_STOP_DISCRETE = 0x4
+DFA_FLAG_BUCKETED = 0x8
+DFA_FLAG_GATHER = 0x10
 DFA_REQ_MINIMISE, DFA_REQ_EQUIVALENT = 0, 1
 
 
@@ -92,7 +94,6 @@ _SIGS = [
     ("dfa_minimise_result", c_int, [c_void_p, POINTER(DfaResult), c_void_p]),
     ("dfa_trans_workspace_size", c_size_t, [POINTER(DfaT), c_void_p]),
     ("dfa_trans", c_int, [POINTER(DfaT), c_void_p, POINTER(c_uint32), c_void_p, c_size_t, c_void_p]),
-    ("dfa_probe_l2_gather", c_int, [c_void_p, c_size_t, c_uint64, c_void_p, POINTER(c_double)]),
     ("dfa_last_error", ctypes.c_char_p, []),
     ("dfa_version", ctypes.c_char_p, []),
 ]
@@ -475,17 +476,6 @@ def trans(delta, accept, workspace=None, stream=None):
     if st != DFA_OK:
         raise DfaError(st, last_error())
     return out, it.value
-
-
-def probe_l2_gather(table, reads: int = 1 << 28, stream=None) -> float:
-    """Random 4-byte reads per second from `table` (a device tensor whose byte
-    size is a power of two; 64 MiB stays in L2): dfa_probe_l2_gather."""
-    rate = c_double(0.0)
-    st = lib().dfa_probe_l2_gather(_ptr(table), int(table.numel() * table.element_size()), int(reads),
-                                   _stream(stream), ctypes.byref(rate))
-    if st != DFA_OK:
-        raise DfaError(st, last_error())
-    return rate.value
 
 
 def header_functions() -> list[str]:

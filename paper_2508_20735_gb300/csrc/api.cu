@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "../../include/dfa.h"
@@ -70,25 +71,121 @@ int check_dfa(const dfa_t *d, const char *name) {
 // ------------------------------------------------------------------ Moore workspace
 static constexpr size_t kMaxGrid = 8192;
 
-// Warps of the Moore kernel's cooperative grid (the largest grid any width
-// uses); without a visible device, the largest grid the launcher accepts.
-static size_t moore_max_warps() {
-  static size_t cached = 0;
-  if (cached) return cached;
-  size_t best = 0;
+// Per-device launch facts of the Moore kernels, looked up once per device
+// (under a mutex: calls may come from several host threads).
+struct DeviceFacts {
+  bool known;
+  int sms;                 // multiprocessors
+  size_t warps;            // warps of the largest cooperative grid any Moore kernel uses
+};
+static constexpr int kMaxDevices = 64;
+static std::mutex g_facts_mu;
+static DeviceFacts g_facts[kMaxDevices];
+
+// Without a visible device: the largest grid the launcher accepts, 148 SMs.
+static DeviceFacts device_facts() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return DeviceFacts{false, 148, kMaxGrid * 16};
+  }
+  std::lock_guard<std::mutex> lock(g_facts_mu);
+  if (g_facts[dev].known) return g_facts[dev];
+  DeviceFacts f{false, 148, 0};
+  if (cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return DeviceFacts{false, 148, kMaxGrid * 16};
+  }
   for (uint32_t v : {1u, 2u, 4u}) {
     LaunchInfo li{};
     if (moore_grid(v, &li) != cudaSuccess) {
       cudaGetLastError();
-      return kMaxGrid * 16;
+      return DeviceFacts{false, f.sms, kMaxGrid * 16};
     }
-    best = std::max(best, (size_t)li.grid * (li.block / 32));
+    f.warps = std::max(f.warps, (size_t)li.grid * (li.block / 32));
   }
-  cached = best;
-  return best;
+  // the bucketed kernel: one block of 1024 threads per SM
+  f.warps = std::max(f.warps, (size_t)f.sms * 32);
+  f.known = true;
+  g_facts[dev] = f;
+  return f;
 }
 
-MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_accept, bool stage_out) {
+static size_t moore_max_warps() { return device_facts().warps; }
+
+// ------------------------------------------------------------------ bucketed gather plan
+static constexpr size_t kBucketSmem = 200 * 1024;   // dynamic shared memory of the bucketed kernel
+static constexpr uint64_t kBucketMaxStates = 1u << 26;
+static constexpr uint32_t kBucketMaxLetters = 16;
+static constexpr size_t kStreamRingBytes = 4 * 2048 * 6;   // assemble: 4 stages of 2048 (es, val) entries
+static constexpr size_t kDedupBytes = ((1u << 15) + (1u << 15) / 32) * 4;   // dedup hash set + duplicate bits
+
+// Bucket sizes for n states, k letters on a grid of `grid` blocks, within
+// the shared memory of one block:
+//   prep      2 counters per target bucket + the region being built (4 bytes an entry);
+//   gather    BT labels + the bucket's segment table (8 bytes per source bucket);
+//   assemble  per state of a source bucket max(4k, 8) bytes of tile (and sort)
+//             and 4 of own label or hash; the region stream's ring; 8 bytes
+//             per partition;
+//   dedup     a partition's hashes (pcap words), 2^15 set slots, duplicate bits.
+// Source buckets are as large as the assemble pass allows, target buckets as
+// large as the gather pass then allows; both counts are rounded to a multiple
+// of the grid so that every block gets the same number of buckets.  BS and BT
+// are multiples of 8 (aligned bulk copies).  Partitions hold about 8 K hashes
+// (a quarter more room, plus 256, before a partition overflows).
+static bool bucket_plan(uint64_t n, uint32_t k, uint64_t grid, BucketPlan *bp) {
+  if (k < 1 || k > kBucketMaxLetters || n < 1 || n > kBucketMaxStates || grid < 1) return false;
+  BucketPlan b{};
+  uint32_t pbits = 0;
+  while (((n + (1ull << pbits) - 1) >> pbits) > 8192) ++pbits;
+  b.pbits = pbits;
+  b.P = 1u << pbits;
+  const uint64_t per = (n + b.P - 1) / b.P;
+  b.pcap = (uint32_t)((per + per / 4 + 256 + 7) / 8 * 8);
+  const size_t dedup = (size_t)b.pcap * 4 + kDedupBytes;
+  // source buckets
+  const uint64_t tw = std::max<uint64_t>(4ull * k, 8) + 4;
+  const uint64_t fixed = kStreamRingBytes + 8ull * b.P + 64;
+  if (fixed >= kBucketSmem) return false;
+  uint64_t bs_max = std::min<uint64_t>({(kBucketSmem - fixed) / tw, 65534 / k, 16384});
+  bs_max = bs_max / 8 * 8;
+  const uint64_t mS = (n + grid * bs_max - 1) / (grid * bs_max);
+  uint64_t BS = (n + grid * mS - 1) / (grid * mS);
+  BS = (BS + 7) / 8 * 8;
+  b.BS = (uint32_t)BS;
+  b.NS = (uint32_t)((n + BS - 1) / BS);
+  // target buckets: labels beside the segment table
+  if (8ull * b.NS + 64 >= kBucketSmem) return false;
+  const uint64_t bt_max = std::min<uint64_t>(65528, (kBucketSmem - 8ull * b.NS - 64) / 4) / 8 * 8;
+  if (bt_max < 8) return false;
+  const uint64_t mT = (n + grid * bt_max - 1) / (grid * bt_max);
+  uint64_t BT = (n + grid * mT - 1) / (grid * mT);
+  BT = (BT + 7) / 8 * 8;
+  b.BT = (uint32_t)BT;
+  b.NT = (uint32_t)((n + BT - 1) / BT);
+  b.cap = (uint32_t)(((uint64_t)k * BS + 7ull * b.NT + 7) / 8 * 8);
+  const size_t prep = 8ull * ((b.NT + 3) / 4 * 4) + 4ull * b.cap;
+  const size_t gather = (size_t)BT * 4 + 8ull * b.NS;
+  const size_t assemble = (size_t)(std::max<uint64_t>(k, 2) * BS + BS + 2ull * b.P) * 4 + kStreamRingBytes;
+  b.smem = std::max({prep, gather, assemble, dedup});
+  // the device divides by BT with a 48-bit reciprocal: products stay below NT * 2^48 < 2^64
+  if (b.smem > kBucketSmem || b.NT >= (1u << 15) || b.pcap >= (1u << 15) * 2 / 3) return false;
+  if ((uint64_t)b.NS * b.cap >= (1ull << 32)) return false;   // entry indices are 32-bit
+  *bp = b;
+  return true;
+}
+
+// Opt-in: on GB300 the direct label reads (served by L2 at its random-request
+// rate) measured faster than the bucketed passes at every size tried, 2^23 to
+// 2^26 states with 4 letters.
+bool choose_bucket(uint64_t n, uint32_t k, uint32_t flags, BucketPlan *bp) {
+  if ((flags & DFA_FLAG_GATHER) || !(flags & DFA_FLAG_BUCKETED)) return false;
+  (void)n;
+  return bucket_plan(n, k, (uint64_t)device_facts().sms, bp);
+}
+
+MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_accept, bool stage_out,
+                         const BucketPlan *bp) {
   MooreLayout L{};
   L.log2S = ceil_log2(n * 2 < 64 ? 64 : n * 2);
   L.mbits = L.log2S + 2 < 31 ? L.log2S + 2 : 31;
@@ -127,6 +224,20 @@ MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_ac
   L.delta = stage_delta ? take((size_t)k * n * 4) : SIZE_MAX;
   L.accept = stage_accept ? take(n) : SIZE_MAX;
   L.out = stage_out ? take(n * 4) : SIZE_MAX;
+  if (bp) {
+    L.bucket = true;
+    L.plan = *bp;
+    const size_t entries = (size_t)bp->NS * bp->cap;
+    L.et = take(entries * 2);
+    L.es = take(entries * 2);
+    L.val = take(entries * 4);
+    L.seg = take((size_t)bp->NT * bp->NS * 8);
+    L.used = take((size_t)bp->NS * 4);
+    L.phash = take((size_t)bp->P * bp->pcap * 4);
+    L.pq = take((size_t)bp->P * bp->pcap * 4);
+    L.pcnt = take((size_t)bp->P * 4);
+    L.list = take(n * 4);
+  }
   L.total = off;
   return L;
 }
@@ -183,10 +294,33 @@ int enqueue_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t
     a.sep_b = track->b;
     a.early_exit = track->early_exit;
   }
+  if (L.bucket) {
+    const BucketPlan &b = L.plan;
+    a.bucket = 1;
+    a.vec = 1;
+    a.B_smem = b.smem;
+    a.B.NT = b.NT;
+    a.B.BT = b.BT;
+    a.B.NS = b.NS;
+    a.B.BS = b.BS;
+    a.B.cap = b.cap;
+    a.B.P = b.P;
+    a.B.pbits = b.pbits;
+    a.B.pcap = b.pcap;
+    a.B.et = reinterpret_cast<uint16_t *>(ws + L.et);
+    a.B.es = reinterpret_cast<uint16_t *>(ws + L.es);
+    a.B.val = reinterpret_cast<uint32_t *>(ws + L.val);
+    a.B.seg = reinterpret_cast<uint2 *>(ws + L.seg);
+    a.B.used = reinterpret_cast<uint32_t *>(ws + L.used);
+    a.B.phash = reinterpret_cast<uint32_t *>(ws + L.phash);
+    a.B.pq = reinterpret_cast<uint32_t *>(ws + L.pq);
+    a.B.pcnt = reinterpret_cast<uint32_t *>(ws + L.pcnt);
+    a.B.list = reinterpret_cast<uint32_t *>(ws + L.list);
+  }
   cudaError_t e = cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ctrl)");
   LaunchInfo li{};
-  e = moore_grid(a.vec, &li);
+  e = moore_grid(a.vec, &li, a.bucket ? a.B_smem : 0);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   if ((size_t)li.grid > kMaxGrid) return fail(DFA_ECUDA, "grid of %d blocks exceeds %zu", li.grid, kMaxGrid);
   e = launch_moore(a, st, &li);
@@ -317,7 +451,11 @@ size_t dfa_workspace_size(const dfa_t *d, const dfa_opts *opts) {
   const dfa_opts o = default_opts(opts);
   const bool hd = d->k > 0 && !is_device_ptr(d->delta);
   const bool ha = !is_device_ptr(d->accept);
-  if (o.algo == DFA_ALGO_MOORE) return moore_layout(d->n, d->k, hd, ha, true).total;
+  if (o.algo == DFA_ALGO_MOORE) {
+    BucketPlan bp{};
+    const bool bucket = choose_bucket(d->n, d->k, o.flags, &bp);
+    return moore_layout(d->n, d->k, hd, ha, true, bucket ? &bp : nullptr).total;
+  }
   if (o.algo == DFA_ALGO_CLOSURE_MOORE) return closure_moore_layout(d->n, d->k, hd, ha).total;
   if (o.algo == DFA_ALGO_SORT) return sort_workspace_size(d, hd, ha, true);
   return naive_workspace_size(d, o);
@@ -342,7 +480,9 @@ int dfa_minimise(const dfa_t *d, const dfa_opts *opts, uint32_t *block_out, dfa_
   const bool hd = d->k > 0 && !is_device_ptr(d->delta);
   const bool ha = !is_device_ptr(d->accept);
   const bool ho = !is_device_ptr(block_out);
-  const MooreLayout L = moore_layout(d->n, d->k, hd, ha, true);
+  BucketPlan bp{};
+  const bool bucket = choose_bucket(d->n, d->k, o.flags, &bp);
+  const MooreLayout L = moore_layout(d->n, d->k, hd, ha, true, bucket ? &bp : nullptr);
   if (ws_bytes < L.total) return fail(DFA_EINVAL, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
   char *ws = static_cast<char *>(workspace);
   const uint32_t *delta = d->delta;

@@ -16,6 +16,9 @@ struct MooreLayout {
   uint32_t log2S, mbits, wid, ebits;
   size_t ctrl, table, lab0, lab1, tmp, minrep, flag, partials, bm0, bm1, seen1, seen2, seen3, seen4, tmp2, rep, dups, dups2, wcnt, delta, accept, out,
       total;
+  bool bucket;             // the bucketed gather runs (plan below); its buffers follow
+  BucketPlan plan;
+  size_t et, es, val, seg, used, phash, pq, pcnt, list;
 };
 
 // Equivalence by union: the two start states whose blocks are compared.
@@ -31,7 +34,12 @@ dfa_opts default_opts(const dfa_opts *o);
 int check_dfa(const dfa_t *d, const char *name);
 bool aligned(const void *p, size_t a);
 uint32_t pick_vec(uint32_t n, uint32_t k, const void *delta, const void *accept, int32_t schedule);
-MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_accept, bool stage_out);
+// bp: the bucketed gather's plan (its buffers are added), or NULL
+MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_accept, bool stage_out,
+                         const BucketPlan *bp = nullptr);
+// Whether signature refinement of n states, k letters and these DFA_FLAG_*
+// flags takes the bucketed gather on the current device, and its plan.
+bool choose_bucket(uint64_t n, uint32_t k, uint32_t flags, BucketPlan *bp);
 // independent_letters: the letters are the DFA's own (not closure letters, which are
 // powers of the same letter), so the sparse-signature estimate may pick filter rounds
 int run_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t n, uint32_t k, uint32_t *out_dev,

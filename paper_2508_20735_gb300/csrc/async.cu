@@ -22,7 +22,9 @@ int dfa_minimise_async(const dfa_t *d, const dfa_opts *opts, uint32_t *block_out
   const bool hd = d->k > 0 && !is_device_ptr(d->delta);
   const bool ha = !is_device_ptr(d->accept);
   const bool ho = !is_device_ptr(block_out);
-  const MooreLayout L = moore_layout(d->n, d->k, hd, ha, true);
+  BucketPlan bp{};
+  const bool bucket = choose_bucket(d->n, d->k, o.flags, &bp);
+  const MooreLayout L = moore_layout(d->n, d->k, hd, ha, true, bucket ? &bp : nullptr);
   if (ws_bytes < L.total) return fail(DFA_EINVAL, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
   if (L.ctrl != 0) return fail(DFA_ECUDA, "control block not at the workspace's start (internal error)");
   char *ws = static_cast<char *>(workspace);

@@ -19,6 +19,8 @@ enum : uint32_t {
   ERR_TABLE_FULL = 4u,     // no free slot (cannot happen with the sizing used)
 };
 
+static constexpr uint32_t kTraceLen = 96;
+
 // Control block at the start of every workspace (zeroed by the host before launch).
 struct Ctrl {
   uint32_t bar_count;      // grid barrier: arrivals in the current generation
@@ -40,12 +42,25 @@ struct Ctrl {
   uint32_t nstill;         // filter rounds: listed states left for the exact table
   unsigned long long t_start, t_end;
   unsigned long long deadline;  // absolute %globaltimer value
+  uint32_t ntrace;         // entries of trace in use
+  uint32_t pad_;
+  unsigned long long trace[kTraceLen];  // (ns since t_start) << 8 | tag, at the phase ends of a launch
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Records the end of a phase (tag < 256) in the control block; called by one
+// thread after a grid barrier, so entries are ordered in time.
+__device__ __forceinline__ void trace_mark(Ctrl *c, uint32_t tag) {
+  const uint32_t i = c->ntrace;
+  if (i < kTraceLen) {
+    c->trace[i] = ((gtimer() - c->t_start) << 8) | tag;
+    c->ntrace = i + 1;
+  }
 }
 
 // B^(k+1) >= 64 n: the previous round's B blocks allow far more signatures
@@ -113,6 +128,63 @@ __device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long limit_ns) 
   }
   __syncthreads();
   return s_ok != 0u;
+}
+
+// ----------------------------------------------------------------- bulk copies (TMA) into shared memory
+// One thread arms an mbarrier with the byte count and issues
+// cp.async.bulk (global -> shared, 16-byte aligned addresses, size a multiple
+// of 16); every thread waits on the barrier's phase.  Waits are bounded: a
+// copy that does not land within limit_ns sets ERR_TIMEOUT (the next grid
+// barrier then ends the launch).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// orders this thread's earlier generic-proxy shared-memory accesses before
+// later bulk copies into the same memory
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// The pieces of bulk_load for a barrier that several copies complete: one
+// arrival announcing the bytes of all of them, then the copies.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0u;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, Ctrl *c,
+                                          unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (gtimer() - t0 > limit_ns) {
+      atomicOr(&c->err, ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
 }
 
 // ----------------------------------------------------------------- L2 cache policies

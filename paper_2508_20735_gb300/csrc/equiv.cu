@@ -52,12 +52,14 @@ using namespace dfa;
 extern "C" {
 
 size_t dfa_equivalent_workspace_size(const dfa_t *a, const dfa_t *b, const dfa_opts *opts) {
-  (void)opts;
   if (check_dfa(a, "a") != DFA_OK || check_dfa(b, "b") != DFA_OK) return 0;
   if (a->k != b->k) return 0;
   const uint64_t n_u = (uint64_t)a->n + b->n;
   if (n_u > DFA_MAX_STATES) return 0;
-  return moore_layout(n_u, a->k, true, true, true).total + kUnionExtra;
+  const dfa_opts o = default_opts(opts);
+  BucketPlan bp{};
+  const bool bucket = choose_bucket(n_u, a->k, o.flags, &bp);
+  return moore_layout(n_u, a->k, true, true, true, bucket ? &bp : nullptr).total + kUnionExtra;
 }
 
 int dfa_equivalent(const dfa_t *a, const dfa_t *b, const dfa_opts *opts, int *equivalent, dfa_result *res,
@@ -74,7 +76,9 @@ int dfa_equivalent(const dfa_t *a, const dfa_t *b, const dfa_opts *opts, int *eq
   const uint32_t n_u = (uint32_t)n_u64, k = a->k;
   const dfa_opts o = default_opts(opts);
   if (o.algo != DFA_ALGO_MOORE) return fail(DFA_EINVAL, "equivalence uses signature refinement (algo 0)");
-  const MooreLayout L = moore_layout(n_u, k, true, true, true);
+  BucketPlan bp{};
+  const bool bucket = choose_bucket(n_u, k, o.flags, &bp);
+  const MooreLayout L = moore_layout(n_u, k, true, true, true, bucket ? &bp : nullptr);
   const size_t need = L.total + kUnionExtra;
   if (ws_bytes < need) return fail(DFA_EINVAL, "workspace too small: %zu < %zu bytes", ws_bytes, need);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -46,6 +46,35 @@ inline __host__ __device__ StagePlan make_plan(uint32_t k, uint32_t bits, uint32
 }
 
 
+// Bucketed signature gather (large state spaces).  δ is re-sorted once per
+// call: states are cut into NS source buckets of BS states and NT target
+// buckets of BT states; the transitions of source bucket s whose target lies
+// in target bucket T form segment (s, T), stored inside region s (cap entries)
+// at seg[T*NS + s].x with seg[T*NS + s].y transitions, padded to a multiple of
+// 8 entries.  Per entry: et = target - T*BT, es = a*BS + (source - s*BS), or
+// kBucketPad for padding.  Each round a pass per target bucket writes the
+// target's label into val (same index); a pass per source bucket reads its
+// region back into a signature tile in shared memory.
+struct BucketArgs {
+  uint32_t NT, BT, NS, BS, cap;
+  uint16_t *et, *es;       // NS*cap
+  uint32_t *val;           // NS*cap: gathered labels of the current round
+  uint2 *seg;              // NT*NS: {offset in region s, transitions}
+  uint32_t *used;          // NS: padded entries of region s
+  // uniqueness test of filter rounds: signature hashes split into P = 2^pbits
+  // partitions of at most pcap entries, each deduplicated in shared memory
+  uint32_t P, pbits, pcap;
+  uint32_t *phash, *pq;    // P*pcap entries: low word of the signature hash, state
+  uint32_t *pcnt;          // P: entries sent to each partition this round
+  uint32_t *list;          // n: states whose signature is not proved unique
+};
+
+// Sizes of the bucketed gather for one state space (host side).
+struct BucketPlan {
+  uint32_t NT, BT, NS, BS, cap, P, pbits, pcap;
+  size_t smem;             // dynamic shared memory of the bucketed kernel
+};
+
 // Arguments of the Moore (signature refinement) persistent kernel.  One call
 // refines one state space; a batch or a disjoint union is one state space whose
 // per-state data are reached through the segment table.
@@ -85,6 +114,9 @@ struct MooreArgs {
   uint32_t track_pair;     // 1: record the round separating sep_a and sep_b
   uint32_t early_exit;
   uint32_t stop_discrete;  // 1: stop after a round that leaves n blocks (no confirming round)
+  uint32_t bucket;         // 1: bucketed gather (moore_kernel<1, true>; B describes it)
+  BucketArgs B;
+  size_t B_smem;           // its dynamic shared memory (BucketPlan::smem)
 };
 
 struct LaunchInfo {
@@ -92,8 +124,10 @@ struct LaunchInfo {
   int block;
 };
 
-// Grid of the Moore kernel (one cooperative wave) and its launch.
-cudaError_t moore_grid(uint32_t vec, LaunchInfo *info);
+// Grid of the Moore kernel (one cooperative wave) and its launch.  The
+// bucketed kernel (bucket_smem > 0) runs one 1024-thread block per SM with
+// that much dynamic shared memory.
+cudaError_t moore_grid(uint32_t vec, LaunchInfo *info, size_t bucket_smem = 0);
 cudaError_t launch_moore(const MooreArgs &a, cudaStream_t stream, LaunchInfo *info);
 
 }  // namespace dfa

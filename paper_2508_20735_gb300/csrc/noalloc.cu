@@ -13,8 +13,9 @@
 // device address; passing it to a kernel would fault (or, where the GPU can
 // reach host memory, silently touch the wrong memory).  The device address is
 // looked up once per device with cudaGetSymbolAddress, with that device
-// current, on the first call made on it; make that first call before any
-// stream capture.  Calls share the one array and leave their contents in it;
+// current, on the first call made on it.  Every call waits for its stream (it
+// reads the round counts back), so no call may be made while that stream is
+// being captured.  Calls share the one array and leave their contents in it;
 // everything a call needs zeroed is cleared by the call itself.  Calls whose
 // work overlaps on the GPU (different streams, or another host thread) race on
 // the array: serialise them.
@@ -24,9 +25,12 @@
 
 namespace dfa {
 
-// 8 MiB: enough for the Moore kernel's scratch at DFA_NOALLOC_MAX_STATES states
-// (table 2 MiB, slot owners 1 MiB, labels 3 x 256 KiB, bitmaps 0.3 MiB,
-// canonical-numbering scratch 0.6 MiB).
+// 8 MiB: the Moore kernel's scratch at DFA_NOALLOC_MAX_STATES states is about
+// 6.6 MiB on a 152-SM GB300: table 2 MiB, slot owners 1 MiB, labels and
+// filter buckets 4 x 256 KiB, canonical numbering 0.6 MiB, bitmaps 0.3 MiB,
+// and the filter rounds' per-warp lists, 2 x 4 x (n + 32 x (warps + 2)) bytes
+// with 32 warps per SM (1.7 MiB at 152 SMs).  The lists grow with the SM
+// count; a layout that would not fit is rejected with DFA_EINVAL.
 static constexpr size_t kNoallocScratchBytes = 8u << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 

@@ -63,6 +63,20 @@ def test_argument_errors_need_no_gpu(built):
     assert st == g.DFA_EINVAL and "alphabets differ" in g.last_error()
 
 
+def test_noalloc_argument_errors_need_no_gpu(built):
+    """dfa_minimise_noalloc rejects, before any launch, an algorithm other than
+    signature refinement and host (numpy) arrays."""
+    import numpy as np
+    delta = np.zeros((2, 8), np.uint32)
+    acc = np.zeros(8, np.uint8)
+    out = np.zeros(8, np.uint32)
+    d, keep = g.make_dfa(delta, acc)
+    st, _ = g.dfa_minimise_noalloc(d, g.make_opts("closure_moore"), out.ctypes.data, None)
+    assert st == g.DFA_EINVAL and "signature refinement only" in g.last_error()
+    st, _ = g.dfa_minimise_noalloc(d, None, out.ctypes.data, None)
+    assert st == g.DFA_EINVAL and "device pointers" in g.last_error()
+
+
 def test_no_cpu_fallback_in_product_path():
     """The package never imports the oracle and has no numpy refinement code."""
     pkg = os.path.dirname(g.__file__)

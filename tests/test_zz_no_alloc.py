@@ -60,6 +60,32 @@ def test_noalloc_matches_dfa_minimise_twice(g):
             (ref_res.num_blocks, ref_res.rounds_changed, ref_res.rounds_executed)
 
 
+def test_noalloc_small_case_matches_oracle(g):
+    """Independently of the GPU's own dfa_minimise: the canonical partition and
+    round counts of a small planted-redundancy DFA equal the oracle's Moore
+    refinement, on two calls in a row."""
+    import oracle
+    base = dfagen.random_dfa(400, 3, 0.5, 75)
+    A, origin = dfagen.planted_redundancy(base, 5, 76)
+    ref = oracle.moore(A.delta, A.accept)
+    for _ in range(2):
+        st, res, got = _noalloc(g, A)
+        assert st == g.DFA_OK, g.last_error()
+        assert np.array_equal(got, ref.block)
+        assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
+            (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
+
+
+def test_noalloc_at_the_state_limit(g):
+    """Exactly DFA_NOALLOC_MAX_STATES states fit the fixed scratch."""
+    A = dfagen.random_dfa(65_536, 4, 0.5, 77)
+    st, res, got = _noalloc(g, A)
+    assert st == g.DFA_OK, g.last_error()
+    ref_res, ref = _reference(g, A)
+    assert np.array_equal(got, ref)
+    assert res.rounds_executed == ref_res.rounds_executed
+
+
 def test_noalloc_rejects_too_many_states(g):
     A = dfagen.random_dfa(65_537, 2, 0.5, 74)
     st, res, _ = _noalloc(g, A)
