@@ -189,6 +189,40 @@ def test_fig1_claims():
     assert t.num_blocks == 10
 
 
+@pytest.mark.parametrize("m", [6, 8, 10])
+def test_chain_transpr_rounds_closed_form(m):
+    """transPR (Algorithm 5) on the chain with n = 2^m states, under the
+    synchronous min-leader reading of Algorithm 2.  The closure letter a^(2^j)
+    sends i to min(i + 2^j, n - 1) and every b-level sends i to 0, so a
+    non-accepting state differs from its block's leader exactly when some
+    a^(2^j) reaches n - 1 from one of them and not from the other: each round
+    cuts every interval of non-accepting states at one more bit of the distance
+    to n - 1, doubling their number, while {n - 1} stays alone.  Hence
+    B_r = min(2^r + 1, n): m rounds that add blocks, one that confirms,
+    rounds_executed = log2 n + 1 (and the leader-election split gives at most
+    one new block per old block per round, B_r <= 2 B_(r-1))."""
+    n = 1 << m
+    C = dfagen.chain_dfa(n)
+    t = oracle.trans_pr(C.delta, C.accept)
+    assert t.num_blocks == n
+    assert t.counts == [min((1 << r) + 1, n) for r in range(m + 1)] + [n]
+    assert (t.rounds_changed, t.rounds_executed) == (m, m + 1)
+    assert all(b <= 2 * a for a, b in zip(t.counts, t.counts[1:]))
+
+
+def test_fig1_transpr_rounds():
+    """Figure 1's 10-state unary chain (q9 accepting): with the closure
+    (letters a, a^2, a^4, a^8) the min-leader naivePR needs 4 splitting rounds
+    and one confirming round, 5 executed, against 8 + 1 without it."""
+    C = dfagen.fig1_chain()
+    t = oracle.trans_pr(C.delta, C.accept)
+    assert t.num_blocks == 10
+    assert (t.rounds_changed, t.rounds_executed) == (4, 5)
+    assert t.counts == [2, 3, 4, 6, 10, 10]
+    plain = oracle.naive_pr(C.delta, C.accept)
+    assert (plain.rounds_changed, plain.rounds_executed) == (8, 9)
+
+
 @pytest.mark.parametrize("lg", [3, 5, 8, 10])
 def test_chain_closed_forms(lg):
     n = 1 << lg
