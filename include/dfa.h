@@ -115,7 +115,10 @@ typedef struct dfa_opts {
   int32_t algo;            /* dfa_algo */
   uint32_t max_rounds;     /* 0 = no limit; otherwise DFA_EMAXROUNDS after this many rounds */
   uint64_t timeout_ns;     /* 0 = library default (600 s); limit on the whole call's device work */
-  int32_t schedule;        /* -1 = autotune / default; >= 0 selects a kernel schedule (batch) */
+  int32_t schedule;        /* -1 = autotune / default; >= 0 selects a kernel schedule: batch calls,
+                              and for dfa_minimise 1, 2 or 4 forces the cooperative kernel with
+                              that many states per thread (the default runs DFAs of at most
+                              16,384 states in one thread block when they fit, see dfa_minimise) */
   uint32_t flags;          /* DFA_FLAG_* */
 } dfa_opts;
 
@@ -140,7 +143,12 @@ size_t dfa_workspace_size(const dfa_t *dfa, const dfa_opts *opts);
 /* Coarsest partition of all n states of `dfa` (unreachable states are kept;
  * Section 2 treats their removal as a separate pre-processing step).
  * block_out: n uint32 (device or host).  res: host struct.  opts may be NULL
- * (Moore, no round limit, default time limit). */
+ * (Moore, no round limit, default time limit).  Signature refinement of a DFA
+ * of at most 16,384 states runs in one thread block with its labels, table
+ * and (when they fit) transitions in shared memory, when its packed signatures
+ * fit 63 bits or it has at most 4,096 states; larger DFAs, DFA_FLAG_TABLE_ONLY,
+ * DFA_FLAG_BUCKETED and an explicit schedule run the cooperative kernel over
+ * the whole GPU.  The results are the same. */
 int dfa_minimise(const dfa_t *dfa, const dfa_opts *opts, uint32_t *block_out, dfa_result *res,
                  void *workspace, size_t ws_bytes, void *stream);
 

@@ -499,10 +499,19 @@ int dfa_minimise(const dfa_t *d, const dfa_opts *opts, uint32_t *block_out, dfa_
     accept = reinterpret_cast<const uint8_t *>(ws + L.accept);
   }
   uint32_t *out = ho ? reinterpret_cast<uint32_t *>(ws + L.out) : block_out;
-  const uint32_t vec_ok = pick_vec(d->n, d->k, delta, accept, o.schedule);
   Ctrl c{};
-  rc = run_moore(delta, accept, d->n, d->k, out, L, ws, o, st, nullptr, &c, vec_ok);
-  if (rc != DFA_OK) return rc;
+  if (small_fits(d->n, d->k, o)) {   // one thread block, everything in shared memory
+    Ctrl *cd = reinterpret_cast<Ctrl *>(ws + L.ctrl);
+    rc = enqueue_small(delta, accept, d->n, d->k, out, cd, o, st);
+    if (rc != DFA_OK) return rc;
+    e = cudaMemcpyAsync(&c, cd, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "single-block refinement kernel");
+  } else {
+    const uint32_t vec_ok = pick_vec(d->n, d->k, delta, accept, o.schedule);
+    rc = run_moore(delta, accept, d->n, d->k, out, L, ws, o, st, nullptr, &c, vec_ok);
+    if (rc != DFA_OK) return rc;
+  }
   const int status = status_from_ctrl(c);
   if (res) {
     res->num_blocks = c.num_blocks;

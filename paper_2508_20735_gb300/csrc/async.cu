@@ -42,8 +42,11 @@ int dfa_minimise_async(const dfa_t *d, const dfa_opts *opts, uint32_t *block_out
   }
   if (e != cudaSuccess) return cuda_fail(e, "copy inputs to device");
   uint32_t *out = ho ? reinterpret_cast<uint32_t *>(ws + L.out) : block_out;
-  rc = enqueue_moore(delta, accept, d->n, d->k, out, L, ws, o, st, nullptr, pick_vec(d->n, d->k, delta, accept,
-                                                                                      o.schedule));
+  if (small_fits(d->n, d->k, o))
+    rc = enqueue_small(delta, accept, d->n, d->k, out, reinterpret_cast<Ctrl *>(ws + L.ctrl), o, st);
+  else
+    rc = enqueue_moore(delta, accept, d->n, d->k, out, L, ws, o, st, nullptr,
+                       pick_vec(d->n, d->k, delta, accept, o.schedule));
   if (rc != DFA_OK) return rc;
   if (ho) {
     e = cudaMemcpyAsync(block_out, out, (size_t)d->n * 4, cudaMemcpyDeviceToHost, st);

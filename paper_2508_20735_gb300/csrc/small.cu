@@ -1,0 +1,333 @@
+// Signature refinement of a small DFA in one thread block.
+//
+// Algorithm 4 (Section 3.3) on a state space that fits in shared memory
+// (n <= kSmallMaxStates): the labels of two consecutive rounds (16-bit), the
+// transitions (16-bit targets, when they fit) and the renumbering table live
+// in shared memory, and rounds are separated by __syncthreads instead of
+// grid-wide barriers.  On a cooperative launch over the whole GPU the barriers
+// dominate at this size (about 20 us a round for 10,000 states).
+//
+// Each round renumbers exactly, in one of three ways chosen alike by every
+// thread from the width w of the labels it reads:
+//  * direct  (k+1) w <= log2 T (at most 16): the packed signature is itself
+//            the new label (so every label stays below T); each state sets the
+//            flag of its signature in the table, and the flags set count the
+//            blocks;
+//  * packed  (k+1) w <= 63: the packed signature is the key of a shared-memory
+//            table (one CAS per probe, on 32-bit slots while the key has at most
+//            31 bits, else on 64-bit slots); the new label is its slot;
+//  * compare otherwise: a table slot holds one representative state, and a
+//            state joins a slot only if its full signature (own label and the
+//            label of every successor) equals the representative's, so a hash
+//            collision costs a probe, never a merge; the label is the slot.
+// The final partition is numbered canonically (blocks in order of their
+// smallest state) inside the block.
+#include <algorithm>
+
+#include "api_util.h"
+
+namespace dfa {
+
+static constexpr int kSmallThreads = 1024;
+static constexpr size_t kSmallSmem = 220 * 1024;   // dynamic shared memory the kernel may take
+static constexpr uint32_t kSmallDirectBits = 16;   // direct rounds: labels of at most 16 bits
+
+struct SmallArgs {
+  const uint32_t *delta;   // k*n, letter-major
+  const uint8_t *accept;   // n
+  uint32_t n, k;
+  uint32_t *out;           // n: canonical block numbers
+  Ctrl *ctrl;
+  uint32_t log2T;          // table slots 2^log2T >= 1.5 n
+  uint32_t wide_table;     // 1: the table has 64-bit slots (packed rounds possible)
+  uint32_t staged;         // 1: δ is copied into shared memory as 16-bit targets (k n halfwords)
+  uint32_t max_rounds;     // 0 = none
+  uint32_t stop_discrete;  // 1: stop after a round that leaves n blocks
+  unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ uint32_t small_mix(uint32_t h, uint32_t v) {
+  h ^= v + 0x9E3779B9u + (h << 6) + (h >> 2);
+  return h * 0x85EBCA6Bu;
+}
+
+__global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __grid_constant__ SmallArgs A) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ uint32_t s_red[32];
+  __shared__ uint32_t s_flag;   // ERR_BAD_DELTA seen by any thread (read after the round's last barrier)
+  __shared__ uint32_t s_stop;   // the call's time limit ran out (thread 0 decides between rounds)
+  const uint32_t n = A.n, k = A.k, tid = threadIdx.x, bd = blockDim.x;
+  const uint32_t T = 1u << A.log2T, mask = T - 1u;
+  const uint32_t twords = A.wide_table ? 2u * T : T;
+  uint32_t *tbl = sm;                                             // table (also the direct rounds' flags)
+  unsigned long long *tbl64 = reinterpret_cast<unsigned long long *>(sm);
+  uint16_t *lab[2] = {reinterpret_cast<uint16_t *>(sm + twords),
+                      reinterpret_cast<uint16_t *>(sm + twords) + ((n + 1u) & ~1u)};
+  uint16_t *d16 = lab[1] + ((n + 1u) & ~1u);                      // k n halfwords when staged
+  volatile uint32_t *vtbl = tbl;
+  Ctrl *C = A.ctrl;
+  const unsigned long long t0 = gtimer();
+  if (tid == 0) {
+    C->t_start = t0;
+    s_flag = 0u;
+  }
+  __syncthreads();   // s_flag is clear before any thread reports into it
+  // the initial partition {F, Q \ F}: labels 0/1, B_0 = the classes present
+  uint32_t seen = 0;
+  for (uint32_t q = tid; q < n; q += bd) {
+    const uint32_t f = A.accept[q] != 0;
+    lab[0][q] = (uint16_t)f;
+    seen |= f ? 1u : 2u;
+  }
+  uint32_t bad = 0;
+  if (A.staged) {   // δ into shared memory, validated once
+    for (size_t i = tid; i < (size_t)k * n; i += bd) {
+      const uint32_t d = A.delta[i];
+      bad |= d >= n;
+      d16[i] = (uint16_t)(d < n ? d : 0u);
+    }
+    if (bad) atomicOr(&s_flag, ERR_BAD_DELTA);
+  }
+  const uint32_t any_acc = block_sum((seen & 1u) ? 1u : 0u, s_red) != 0u;
+  const uint32_t any_rej = block_sum((seen & 2u) ? 1u : 0u, s_red) != 0u;
+  uint32_t B_prev = any_acc + any_rej, B_r = B_prev;
+  uint32_t r = 0, changed = 0, cur = 0, maxed = 0, err = s_flag, w = 1;
+  // δ(q, a): the shared copy, or global memory (an invalid target reads as 0 and is reported)
+  auto target = [&](uint32_t a, uint32_t q) -> uint32_t {
+    if (A.staged) return d16[(size_t)a * n + q];
+    uint32_t d = A.delta[(size_t)a * n + q];
+    if (d >= n) {
+      bad = 1u;
+      d = 0u;
+    }
+    return d;
+  };
+  for (r = 1; !err; ++r) {
+    const uint16_t *src = lab[cur];
+    uint16_t *dst = lab[cur ^ 1u];
+    const uint32_t K = (k + 1u) * w;
+    const uint32_t mode = (K <= kSmallDirectBits && K <= A.log2T) ? 0u : K <= 31u ? 3u : (A.wide_table && K <= 63u) ? 1u : 2u;
+    const uint32_t words = mode == 0u ? (1u << K) : (mode == 1u ? 2u * T : T);   // packed 32-bit keys (3): T words
+    for (uint32_t i = tid; i < words; i += bd) tbl[i] = 0u;
+    __syncthreads();
+    uint32_t created = 0;
+    bad = 0;
+    if (mode == 0u) {   // direct: the signature is the label; a flag per signature present
+      for (uint32_t q = tid; q < n; q += bd) {
+        uint32_t key = src[q];
+        uint32_t shift = w;
+        for (uint32_t a = 0; a < k; ++a) {
+          key |= (uint32_t)src[target(a, q)] << shift;
+          shift += w;
+        }
+        dst[q] = (uint16_t)key;
+        tbl[key] = 1u;   // every writer of a slot writes the same value
+      }
+      __syncthreads();
+      for (uint32_t i = tid; i < (1u << K); i += bd) created += tbl[i];
+    } else if (mode == 1u) {   // packed key, 64-bit slots
+      for (uint32_t q = tid; q < n; q += bd) {
+        unsigned long long key = src[q];
+        uint32_t shift = w;
+        for (uint32_t a = 0; a < k; ++a) {
+          key |= (unsigned long long)src[target(a, q)] << shift;
+          shift += w;
+        }
+        key |= 1ull << 63;   // never 0, the free marker
+        uint32_t slot = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64u - A.log2T));
+        for (uint32_t probe = 0; probe < T; ++probe) {
+          const unsigned long long v = atomicCAS(&tbl64[slot], 0ull, key);
+          if (v == 0ull) {   // q represents a new block
+            ++created;
+            break;
+          }
+          if (v == key) break;   // q joins that block
+          slot = (slot + 1u) & mask;
+        }
+        dst[q] = (uint16_t)slot;
+      }
+    } else if (mode == 3u) {   // packed key of at most 31 bits, 32-bit slots
+      for (uint32_t q = tid; q < n; q += bd) {
+        uint32_t key = src[q];
+        uint32_t shift = w;
+        for (uint32_t a = 0; a < k; ++a) {
+          key |= (uint32_t)src[target(a, q)] << shift;
+          shift += w;
+        }
+        key |= 1u << 31;   // never 0, the free marker
+        uint32_t slot = (key * 0x9E3779B1u) >> (32u - A.log2T);
+        for (uint32_t probe = 0; probe < T; ++probe) {
+          const uint32_t v = atomicCAS(&tbl[slot], 0u, key);
+          if (v == 0u) {   // q represents a new block
+            ++created;
+            break;
+          }
+          if (v == key) break;   // q joins that block
+          slot = (slot + 1u) & mask;
+        }
+        dst[q] = (uint16_t)slot;
+      }
+    } else {   // representative and full comparison
+      for (uint32_t q = tid; q < n; q += bd) {
+        uint32_t h = small_mix(0x3C6EF372u, src[q]);
+        for (uint32_t a = 0; a < k; ++a) h = small_mix(h, src[target(a, q)]);
+        h ^= h >> 15;
+        uint32_t slot = (h * 0x2C1B3C6Du) >> (32u - A.log2T) & mask;
+        for (uint32_t probe = 0; probe < T; ++probe) {
+          uint32_t v = vtbl[slot];
+          if (v == 0u) {
+            v = atomicCAS(&tbl[slot], 0u, q + 1u);
+            if (v == 0u) {   // q represents a new block
+              ++created;
+              break;
+            }
+          }
+          const uint32_t p = v - 1u;
+          bool same = src[q] == src[p];
+          for (uint32_t a = 0; same && a < k; ++a) same = src[target(a, q)] == src[target(a, p)];
+          if (same) break;   // q joins that block
+          slot = (slot + 1u) & mask;
+        }
+        dst[q] = (uint16_t)slot;
+      }
+    }
+    if (bad) atomicOr(&s_flag, ERR_BAD_DELTA);
+    B_r = block_sum(created, s_red);   // includes the barriers that end the round
+    cur ^= 1u;
+    w = mode == 0u ? K : A.log2T;   // table rounds: labels are slots
+    if (s_flag) {   // every thread reads it after the same barrier: a uniform decision
+      err = s_flag;
+      break;
+    }
+    const bool grew = B_r != B_prev;
+    if (grew) ++changed;
+    if (!grew) break;   // Algorithm 4's until-test: the round added no block
+    if (A.stop_discrete && B_r == n) break;
+    if (A.max_rounds != 0u && r >= A.max_rounds) {
+      maxed = 1u;
+      break;
+    }
+    // the call's time limit, every 16 rounds: thread 0 decides, every thread reads it after a barrier
+    if ((r & 15u) == 0u) {
+      if (tid == 0) s_stop = gtimer() - t0 > A.timeout_ns ? 1u : 0u;
+      __syncthreads();
+      if (s_stop) {
+        err = ERR_TIMEOUT;
+        break;
+      }
+    }
+    B_prev = B_r;
+  }
+  if (err) {
+    if (tid == 0) {
+      C->err = err;
+      C->t_end = gtimer();
+    }
+    return;
+  }
+  // canonical numbering: blocks in order of their smallest state (every label
+  // is below T: a slot, or a direct signature of at most log2 T bits)
+  const uint16_t *fin = lab[cur];
+  uint32_t blocks = B_r;
+  if (B_r == n) {
+    for (uint32_t q = tid; q < n; q += bd) A.out[q] = q;
+  } else {
+    uint16_t *rank = lab[cur ^ 1u];   // free now: rank of each block's smallest state
+    for (uint32_t i = tid; i < T; i += bd) tbl[i] = 0xFFFFFFFFu;
+    __syncthreads();
+    for (uint32_t q = tid; q < n; q += bd) atomicMin(&tbl[fin[q]], q);
+    __syncthreads();
+    const uint32_t per = (n + bd - 1) / bd;
+    const uint32_t q0 = tid * per < n ? tid * per : n, q1 = q0 + per < n ? q0 + per : n;
+    uint32_t c = 0;
+    for (uint32_t q = q0; q < q1; ++q) c += tbl[fin[q]] == q;
+    uint32_t total;
+    uint32_t base = block_excl_scan(c, s_red, &total);
+    for (uint32_t q = q0; q < q1; ++q)
+      if (tbl[fin[q]] == q) rank[q] = (uint16_t)base++;
+    __syncthreads();
+    for (uint32_t q = tid; q < n; q += bd)
+      if (tbl[fin[q]] == q) tbl[fin[q]] = 0x80000000u | rank[q];
+    __syncthreads();
+    for (uint32_t q = tid; q < n; q += bd) A.out[q] = tbl[fin[q]] & 0x7FFFFFFFu;
+    blocks = total;
+  }
+  if (tid == 0) {
+    C->rounds_executed = r;
+    C->rounds_changed = changed;
+    C->num_blocks = blocks;
+    C->maxed = maxed;
+    C->t_end = gtimer();
+  }
+}
+
+// Shared memory of the kernel for n states and k letters (smem 0: no fit).
+struct SmallPlan {
+  uint32_t log2T, wide, staged;
+  size_t smem;
+};
+
+static SmallPlan small_plan(uint32_t n, uint32_t k) {
+  SmallPlan p{};
+  p.log2T = ceil_log2(n + n / 2 < 64 ? 64 : n + n / 2);
+  const size_t T = (size_t)1 << p.log2T;
+  const size_t labels = 2 * (size_t)((n + 1u) & ~1u) * 2;
+  p.wide = (uint64_t)(k + 1) * p.log2T <= 63 ? 1u : 0u;
+  size_t table = T * (p.wide ? 8 : 4);   // also the direct rounds' flags (2^log2T words at most)
+  if (table + labels > kSmallSmem && p.wide) {   // 64-bit slots do not fit: representatives
+    p.wide = 0;
+    table = T * 4;
+  }
+  p.smem = table + labels;
+  if (p.smem > kSmallSmem) {
+    p.smem = 0;
+    return p;
+  }
+  if (p.smem + (size_t)k * n * 2 <= kSmallSmem) {
+    p.staged = 1;
+    p.smem += (size_t)k * n * 2;
+  }
+  return p;
+}
+
+// The single block is taken where it measured faster than the cooperative
+// kernel: when packed keys fit 64-bit slots, or up to 4,096 states whatever
+// the letters.  An explicit `schedule` (a width of the cooperative kernel),
+// the table-only and bucketed flags keep the cooperative kernel.
+bool small_fits(uint32_t n, uint32_t k, const dfa_opts &o) {
+  if (o.algo != DFA_ALGO_MOORE) return false;
+  if (o.schedule >= 1) return false;
+  if (o.flags & (DFA_FLAG_BUCKETED | DFA_FLAG_TABLE_ONLY)) return false;
+  if (n < 1 || n > kSmallMaxStates) return false;
+  const SmallPlan p = small_plan(n, k);
+  return p.smem != 0 && (p.wide || n <= 4096);
+}
+
+int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
+                  const dfa_opts &o, cudaStream_t st) {
+  const SmallPlan p = small_plan(n, k);
+  if (p.smem == 0) return fail(DFA_EINVAL, "the single-block kernel does not fit %u states", n);
+  SmallArgs a{};
+  a.delta = delta;
+  a.accept = accept;
+  a.n = n;
+  a.k = k;
+  a.out = out;
+  a.ctrl = ctrl;
+  a.log2T = p.log2T;
+  a.wide_table = p.wide;
+  a.staged = p.staged;
+  a.max_rounds = o.max_rounds;
+  a.stop_discrete = (o.flags & DFA_FLAG_STOP_DISCRETE) ? 1u : 0u;
+  a.timeout_ns = o.timeout_ns;
+  cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ctrl)");
+  e = cudaFuncSetAttribute(moore_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e != cudaSuccess) return cuda_fail(e, "shared memory of the single-block kernel");
+  moore_small_kernel<<<1, kSmallThreads, p.smem, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "launch of the single-block kernel");
+  return DFA_OK;
+}
+
+}  // namespace dfa

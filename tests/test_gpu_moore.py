@@ -56,6 +56,33 @@ def test_random_sizes_ragged(g, n, k):
     _assert_parity(g, A)
 
 
+@pytest.mark.parametrize("n", [1, 2, 7, 63, 65, 513, 4097, 10_000, 16_384])
+@pytest.mark.parametrize("k", [0, 2, 5])
+def test_small_sizes_both_kernels(g, n, k):
+    """Up to 16,384 states the default call runs the single-block kernel; an
+    explicit schedule (1) runs the cooperative kernel.  Both equal the oracle."""
+    A = dfagen.random_dfa(n, k, 0.5, 5000 + n + k)
+    ref = oracle.moore(A.delta, A.accept)
+    _assert_parity(g, A, ref)
+    _assert_parity(g, A, ref, schedule=1)
+
+
+def test_small_kernel_deep_chain_and_limits(g):
+    """The single-block kernel on the 16,384-state chain: 16,383 rounds to the
+    fixpoint; a round limit and a time limit end it with their statuses."""
+    C = dfagen.chain_dfa(16_384)
+    res = _assert_parity(g, C)
+    assert res.rounds_changed == 16_382
+    d, a = _dev(C)
+    block, res = g.minimise(d, a, max_rounds=7, check=False)
+    assert res.call_status == g.DFA_EMAXROUNDS and res.rounds_executed == 7
+    ref = oracle.moore(C.delta, C.accept, max_rounds=7)
+    assert np.array_equal(block.cpu().numpy().view(np.uint32), oracle.canonical(ref.block))
+    _, res = g.minimise(d, a, timeout_ns=200_000, check=False)    # 0.2 ms: far below the work needed
+    assert res.call_status == g.DFA_ETIMEOUT
+    _assert_parity(g, dfagen.random_dfa(4096, 2, 0.5, 1))          # the context survives
+
+
 @pytest.mark.parametrize("schedule", [1, 2, 4])
 @pytest.mark.parametrize("n,k", [(4096, 2), (100_000, 4), (30_001, 3)])
 def test_vector_widths(g, schedule, n, k):
