@@ -11,8 +11,9 @@ N > 1 (torchrun, one process per GPU): every rank refines its own copy of the
 workload (independent problems, no collective on the data path); the value
 is the sum over ranks divided by the slowest rank's time ("weak" scaling).
 
---impl reference times the CPU oracle (numpy, the machine's host cores) on a
-bounded sample of the same workload: one refinement round per step.
+--impl reference times the CPU oracle's Moore refinement in plain C with
+OpenMP on all of the machine's host cores (oracle/moore.c), one whole refinement
+of the same workload per step.
 
 Prints one JSON line (rank 0).
 """
@@ -52,6 +53,7 @@ def parse():
                     help="batch: time only the packed batched call on --batch-dfas DFAs of the batch recipe")
     ap.add_argument("--batch-dfas", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=10_000)
+    ap.add_argument("--serve-pairs", type=int, default=1000, help="serve case: distinct generated pairs")
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     ap.add_argument("--schedule", type=int, default=-1, help="batch case: kernel schedule (-1 = autotuned)")
@@ -159,46 +161,64 @@ def host_info():
     return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
 
 
-def cpu_baseline(A, seconds_hint=True):
-    """The oracle as it stands, one Moore round on the full workload (a bounded sample)."""
-    import numpy as np
+def cpu_baseline(A):
+    """The oracle as it stands, on the machine's host cores: the C Moore refinement
+    (oracle/moore.c) with OpenMP on all cores over the whole workload (the
+    baseline proper), beside the same code on one thread (a 2^22-state sample of
+    the recipe, scaled per transition) and one round of the numpy oracle."""
+    import dfagen
     import oracle
+    n, k = A.n, A.k
+    cores = oracle.host_threads()
+    t = time.perf_counter()
+    r = oracle.moore_c(A.delta, A.accept, threads=0)
+    dt = time.perf_counter() - t
+    S = dfagen.random_dfa(1 << 22, k, WORKLOAD["p_accept"], WORKLOAD["seed"])
+    t = time.perf_counter()
+    rs = oracle.moore_c(S.delta, S.accept, threads=1)
+    dt1 = time.perf_counter() - t
     block = oracle.initial_partition(A.accept)
     t = time.perf_counter()
     oracle.moore_round(A.delta, block)
-    dt = time.perf_counter() - t
-    n, k = A.n, A.k
-    return {"value": n * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
-            "sample": f"one signature-refinement round of the numpy oracle on the full {n}-state, {k}-letter DFA "
-                      f"({dt:.1f} s)"}
+    dtn = time.perf_counter() - t
+    return {"value": n * k * r.rounds_executed / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "host": host_info(),
+            "sample": f"oracle/moore.c with OpenMP on {cores} threads: the whole refinement of the {n}-state, "
+                      f"{k}-letter workload ({r.rounds_executed} rounds, {dt:.2f} s)",
+            "single_thread": {"value": S.n * k * rs.rounds_executed / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"oracle/moore.c on one thread, the recipe at 2^22 states "
+                                        f"({rs.rounds_executed} rounds, {dt1:.2f} s)"},
+            "numpy_round": {"value": n * k / dtn, "unit": UNIT, "cores": 1,
+                            "sample": f"one round of the numpy oracle on the full workload ({dtn:.1f} s)"}}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     import dfagen
-    A = dfagen.random_dfa(WORKLOAD["n"], WORKLOAD["k"], WORKLOAD["p_accept"], WORKLOAD["seed"])
     import oracle
-    block = oracle.initial_partition(A.accept)
-    times = []
+    A = dfagen.random_dfa(WORKLOAD["n"], WORKLOAD["k"], WORKLOAD["p_accept"], WORKLOAD["seed"])
+    cores = oracle.host_threads()
+    times, rounds = [], []
     for i in range(args.warmup + args.steps):
         t = time.perf_counter()
-        oracle.moore_round(A.delta, block)
+        r = oracle.moore_c(A.delta, A.accept, threads=0)
         dt = time.perf_counter() - t
         if i >= args.warmup:
             times.append(dt)
+            rounds.append(r.rounds_executed)
     tot = sum(times)
-    value = A.n * A.k * len(times) / tot
+    value = A.n * A.k * sum(rounds) / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": dict(WORKLOAD, parallelism="cpu", step="one oracle refinement round"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one signature-refinement round per step on the full workload"},
+            "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism=f"cpu, {cores} threads", step="one whole oracle refinement"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "oracle/moore.c (OpenMP, all host cores): the whole refinement of the "
+                                       "full workload per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
 
 
 def _dev(A):
@@ -225,15 +245,23 @@ def extras(g):
 
     import dfagen
     out = {}
-    # random DFA, n = 10,000, k = 2 (small: latency-bound)
+    import oracle
+    cores = oracle.host_threads()
+    # random DFA, n = 10,000, k = 2 (small: the single-block kernel), against the cooperative kernel and the C oracle
     A = dfagen.random_dfa(10_000, 2, 0.5, 1)
     d, a = _dev(A)
     res = g.minimise(d, a)[1]
-    dev = []
+    dev, coop = [], []
     for _ in range(20):
         dev.append(g.minimise(d, a)[1].device_ns)
+        coop.append(g.minimise(d, a, schedule=1)[1].device_ns)
+    cpu1 = _best_of(lambda: oracle.moore_c(A.delta, A.accept, threads=1), 5)
+    cpuN = _best_of(lambda: oracle.moore_c(A.delta, A.accept, threads=0), 5)
     out["random_n1e4_k2"] = {"device_us": statistics.median(dev) / 1e3, "rounds": res.rounds_executed,
-                             "transitions_per_s": A.n * A.k * res.rounds_executed / (statistics.median(dev) * 1e-9)}
+                             "kernel": "single thread block (n <= 16,384)",
+                             "cooperative_kernel_device_us": statistics.median(coop) / 1e3,
+                             "transitions_per_s": A.n * A.k * res.rounds_executed / (statistics.median(dev) * 1e-9),
+                             "cpu_oracle_us": {"1_core": cpu1 * 1e6, f"{cores}_cores": cpuN * 1e6}}
     # deep-round chain, n = 2^20: transPR in full; plain refinement over a bounded number of rounds
     C = dfagen.chain_dfa(1 << 20)
     d, a = _dev(C)
@@ -242,10 +270,26 @@ def extras(g):
     bounded = 20_000
     mo = g.minimise(d, a, max_rounds=bounded, check=False)[1]
     us_round = mo.device_ns / 1e3 / mo.rounds_executed
+    t = time.perf_counter()
+    tref = oracle.trans_pr(C.delta, C.accept)
+    trans_cpu = time.perf_counter() - t
+    per_state_round = []
+    for lg in (12, 13, 14):
+        X = dfagen.chain_dfa(1 << lg)
+        t = time.perf_counter()
+        rx = oracle.moore_c(X.delta, X.accept, threads=1)
+        per_state_round.append((time.perf_counter() - t) / rx.rounds_executed / X.n)
+    ns_sr = statistics.median(per_state_round) * 1e9
     out["chain_n2p20"] = {
-        "trans": {"rounds": tr.rounds_executed, "device_ms": tr.device_ns / 1e6, "blocks": tr.num_blocks},
+        "trans": {"rounds": tr.rounds_executed, "device_ms": tr.device_ns / 1e6, "blocks": tr.num_blocks,
+                  "cpu_oracle_s": trans_cpu, "cpu_oracle_rounds": tref.rounds_executed,
+                  "cpu_sample": "numpy oracle transPR (closure + naivePR) at the full 2^20 states, 1 core"},
         "moore": {"rounds_needed": C.n - 1, "rounds_timed": mo.rounds_executed, "us_per_round": us_round,
-                  "projected_s_for_all_rounds": us_round * (C.n - 1) / 1e6},
+                  "projected_s_for_all_rounds": us_round * (C.n - 1) / 1e6,
+                  "cpu_oracle_ns_per_state_round": ns_sr,
+                  "cpu_oracle_projected_s_for_all_rounds": ns_sr * 1e-9 * C.n * (C.n - 1),
+                  "cpu_sample": "oracle/moore.c on one core, whole refinement of the chains 2^12, 2^13, 2^14 "
+                                "(n - 1 rounds each), cost per state and round extrapolated to 2^20"},
     }
     # the minimal DFA itself (reachability + quotient) of the 2^24-state workload, from its partition
     R = dfagen.random_dfa(WORKLOAD["n"], WORKLOAD["k"], WORKLOAD["p_accept"], WORKLOAD["seed"])
@@ -323,58 +367,139 @@ def extras(g):
     tl = _time_calls(lambda: g.minimise_batch(items, out=outb), 3)
     singles = [(x[0], x[1], torch.empty(x[1].numel(), dtype=torch.int32, device="cuda")) for x in items]
     ts = _time_calls(lambda: [g.minimise(x[0], x[1], out=x[2]) for x in singles], 1)
+    sample = dfas[:512]
+    t = time.perf_counter()
+    for X in sample:
+        oracle.moore_c(X.delta, X.accept, threads=1)
+    c1 = len(sample) / (time.perf_counter() - t)
+    from concurrent.futures import ThreadPoolExecutor
+    t = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(lambda X: oracle.moore_c(X.delta, X.accept, threads=1), sample))
+    cN = len(sample) / (time.perf_counter() - t)
     out["batch_4096"] = {"states": int(sum(X.n for X in dfas)), "batched_dfas_per_s": 4096 / tb,
                          "single_launch_dfas_per_s": 4096 / ts, "speedup": ts / tb, "batched_ms": tb * 1e3,
                          "batched_device_ms": dev_ms, "list_form_ms": tl * 1e3,
-                         "form": "packed (dfa_minimise_batch_packed); list_form_ms: one dfa_t per DFA"}
-    # served equivalence stream (bounded sample: requests drawn from a pool of generated pairs whose
-    # arrays sit in pinned host memory, as a server's receive buffers would)
-    def _pinned(X):
-        return (torch.from_numpy(np.ascontiguousarray(X.delta).view(np.int32)).pin_memory(),
-                torch.from_numpy(np.ascontiguousarray(X.accept)).pin_memory(), X.start)
-    pool = [(_pinned(A), _pinned(B), eq) for A, B, eq in (dfagen.equivalence_pair(i, 5) for i in range(24))]
-    nreq = 10_000
-    with g.Server(24 << 30, max_slots=64) as srv:
+                         "form": "packed (dfa_minimise_batch_packed); list_form_ms: one dfa_t per DFA",
+                         "cpu_oracle_dfas_per_s": {"1_core": c1, f"{cores}_cores": cN},
+                         "cpu_sample": "oracle/moore.c, one DFA per thread, the first 512 DFAs of the recipe"}
+    out["serve_equiv"] = serve_study(g, pairs=1000, nreq=10_000)
+    return out
+
+
+def _best_of(fn, reps):
+    best = float("inf")
+    for _ in range(reps):
+        t = time.perf_counter()
+        fn()
+        best = min(best, time.perf_counter() - t)
+    return best
+
+
+def _gen_pair(i):
+    import dfagen
+    A, B, eq = dfagen.equivalence_pair(i, 5)
+    return A.delta, A.accept, A.start, B.delta, B.accept, B.start, eq
+
+
+def make_pair_pool(pairs: int):
+    """`pairs` distinct requests of the served-equivalence recipe (seed 5), generated in a
+    spawn process pool (no CUDA in the workers) before any arrival clock starts."""
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4),
+                             mp_context=multiprocessing.get_context("spawn")) as ex:
+        return list(ex.map(_gen_pair, range(pairs), chunksize=8))
+
+
+def _union(dA, aA, dB, aB):
+    """The disjoint union A ⊎ B as arrays (B's states after A's): the oracle's input for one request."""
+    import numpy as np
+    nA = aA.shape[0]
+    return np.concatenate([dA, dB.astype(np.uint64) + nA], axis=1).astype(np.uint32), np.concatenate([aA, aB])
+
+
+def serve_study(g, pairs: int, nreq: int, loads=(0.5, 0.8, 0.95), slots: int = 64, budget_gb: float = 24.0):
+    """The served-equivalence stream: `nreq` requests drawn round robin from `pairs`
+    distinct generated pairs whose arrays sit in pinned host memory (a server's receive
+    buffers), first in a closed loop (capacity), then with Poisson arrivals at each load
+    (a fraction of that capacity): p50/p99 latency and throughput, verdicts checked
+    against the generator.  Beside it: the same requests through serial dfa_equivalent
+    calls, and the CPU oracle (Moore on the union) per request."""
+    import numpy as np
+    import torch
+
+    import oracle
+    t = time.perf_counter()
+    raw = make_pair_pool(pairs)
+    gen_s = time.perf_counter() - t
+
+    def _pinned(d, acc):
+        return (torch.from_numpy(np.ascontiguousarray(d).view(np.int32)).pin_memory(),
+                torch.from_numpy(np.ascontiguousarray(acc)).pin_memory())
+    pool = [((*_pinned(dA, aA), sA), (*_pinned(dB, aB), sB), eq) for dA, aA, sA, dB, aB, sB, eq in raw]
+    states = float(np.mean([r[1].shape[0] + r[4].shape[0] for r in raw]))
+    with g.Server(int(budget_gb * (1 << 30)), max_slots=slots) as srv:
         t0 = time.perf_counter()
         tickets = [srv.submit_equivalent(A, B) for A, B, _ in (pool[i % len(pool)] for i in range(nreq))]
-        for t in tickets:
-            srv.wait(t)
+        wrong = 0
+        for i, tk in enumerate(tickets):
+            _, _, eq, _ = srv.wait(tk)
+            wrong += int(bool(eq) != pool[i % len(pool)][2])
         cap = nreq / (time.perf_counter() - t0)
         counters = srv.counters()
     rng = np.random.default_rng(5)
-    lam = 0.8 * cap
-    gaps = rng.exponential(1.0 / lam, nreq)
-    wrong = 0
-    with g.Server(24 << 30, max_slots=64) as srv:
-        tickets = []
-        t_next = time.perf_counter()
-        for i in range(nreq):
-            t_next += gaps[i]
-            while time.perf_counter() < t_next:
-                pass
-            A, B, _ = pool[i % len(pool)]
-            tickets.append(srv.submit_equivalent(A, B))
-        for i, t in enumerate(tickets):
-            st, _, eq, _ = srv.wait(t)
-            wrong += int(bool(eq) != pool[i % len(pool)][2])
-        s = srv.stats()
-    # the same requests one after another through dfa_equivalent (the same pinned host inputs)
-    for A, B, _ in pool:
+    points = []
+    for frac in loads:
+        lam = frac * cap
+        gaps = rng.exponential(1.0 / lam, nreq)
+        with g.Server(int(budget_gb * (1 << 30)), max_slots=slots) as srv:
+            tickets = []
+            t_next = time.perf_counter()
+            for i in range(nreq):
+                t_next += gaps[i]
+                while time.perf_counter() < t_next:
+                    pass
+                A, B, _ = pool[i % len(pool)]
+                tickets.append(srv.submit_equivalent(A, B))
+            bad = 0
+            for i, tk in enumerate(tickets):
+                _, _, eq, _ = srv.wait(tk)
+                bad += int(bool(eq) != pool[i % len(pool)][2])
+            st = srv.stats()
+        wrong += bad
+        points.append({"load": frac, "offered_rps": lam, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
+                       "throughput_rps": st["throughput_rps"], "wrong_verdicts": bad})
+    sample = pool[:64]
+    for A, B, _ in sample[:4]:
         g.equivalent(A, B)
     t0 = time.perf_counter()
-    for i in range(2 * len(pool)):
-        A, B, _ = pool[i % len(pool)]
+    for A, B, _ in sample:
         g.equivalent(A, B)
-    serial = 2 * len(pool) / (time.perf_counter() - t0)
-    out["serve_equiv"] = {"requests": nreq, "distinct_pairs": len(pool), "closed_loop_rps": cap,
-                          "serial_dfa_equivalent_rps": serial, "closed_loop_vs_serial": cap / serial,
-                          "offered_rps": lam, "p50_us": s["p50_us"], "p99_us": s["p99_us"],
-                          "throughput_rps": s["throughput_rps"], "wrong_verdicts": wrong,
-                          "closed_loop_counters": counters,
-                          "sample": "Poisson arrivals at 0.8 x closed-loop capacity; pairs of the served-equivalence "
-                                    "recipe (A: n log-uniform in [1e3, 1e6], k in {2, 4}) reused round robin, "
-                                    "inputs in pinned host memory"}
-    return out
+    serial = len(sample) / (time.perf_counter() - t0)
+    unions = [_union(r[0], r[1], r[3], r[4]) for r in raw[:64]]
+    t0 = time.perf_counter()
+    for d, acc in unions:
+        oracle.moore_c(d, acc, threads=1)
+    cpu1 = len(unions) / (time.perf_counter() - t0)
+    from concurrent.futures import ThreadPoolExecutor
+    cores = oracle.host_threads()
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(lambda u: oracle.moore_c(u[0], u[1], threads=1), unions))
+    cpuN = len(unions) / (time.perf_counter() - t0)
+    ms = [counters["state_rounds_direct"], counters["state_rounds_filter"], counters["state_rounds_table"]]
+    return {"requests": nreq, "distinct_pairs": len(pool), "mean_union_states": states,
+            "pool_generation_s": gen_s, "closed_loop_rps": cap, "closed_loop_wrong_verdicts": wrong,
+            "load_points": points, "serial_dfa_equivalent_rps": serial, "closed_loop_vs_serial": cap / serial,
+            "closed_loop_counters": counters,
+            "table_mode_share": ms[2] / max(1, sum(ms)),
+            "cpu_oracle_rps": {"1_core": cpu1, f"{cores}_cores": cpuN},
+            "cpu_sample": "oracle/moore.c on the union A ⊎ B of the first 64 pairs, one request per thread",
+            "sample": f"Poisson arrivals at {', '.join(str(x) for x in loads)} x closed-loop capacity; "
+                      f"{nreq} requests drawn round robin from {len(pool)} distinct pairs of the "
+                      "served-equivalence recipe (A: n log-uniform in [1e3, 1e6], k in {2, 4}; seed 5), "
+                      "inputs in pinned host memory"}
 
 
 def run_batch_case(args, local):
@@ -410,21 +535,21 @@ def run_batch_case(args, local):
 
 def run_serve_case(args, local):
     """The served-equivalence workload alone: each step submits --serve-requests
-    requests (pairs of the served-equivalence recipe, seed 5, drawn round robin
-    from 24 generated pairs whose arrays sit in pinned host memory) to one server
-    and waits for all of them (closed loop)."""
+    requests (drawn round robin from --serve-pairs distinct pairs of the
+    served-equivalence recipe, seed 5, whose arrays sit in pinned host memory) to
+    one server and waits for all of them (closed loop)."""
     import numpy as np
     import torch
 
-    import dfagen
     import paper_2508_20735_gb300 as g
+    raw = make_pair_pool(args.serve_pairs)   # before any CUDA work (spawned workers)
     torch.cuda.set_device(local)
     g.build()
 
-    def _pinned(X):
-        return (torch.from_numpy(np.ascontiguousarray(X.delta).view(np.int32)).pin_memory(),
-                torch.from_numpy(np.ascontiguousarray(X.accept)).pin_memory(), X.start)
-    pool = [(_pinned(A), _pinned(B)) for A, B, _ in (dfagen.equivalence_pair(i, 5) for i in range(24))]
+    def _pinned(d, acc):
+        return (torch.from_numpy(np.ascontiguousarray(d).view(np.int32)).pin_memory(),
+                torch.from_numpy(np.ascontiguousarray(acc)).pin_memory())
+    pool = [((*_pinned(dA, aA), sA), (*_pinned(dB, aB), sB)) for dA, aA, sA, dB, aB, sB, _ in raw]
     nreq = args.serve_requests
     with g.Server(int(args.serve_budget_gb * (1 << 30)), max_slots=args.serve_slots) as srv:
         def step():
@@ -445,6 +570,7 @@ def run_serve_case(args, local):
                       "unit": "requests/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "dtype": "u32",
                       "data": "synthetic", "config": {"workload": f"serve_equiv_{nreq}_requests",
+                                                      "distinct_pairs": len(pool),
                                                       "max_slots": args.serve_slots,
                                                       "hbm_budget_gb": args.serve_budget_gb},
                       "counters": d, "clocks": clk.summary(), "gpu_launches": int(d["steps"])}), flush=True)

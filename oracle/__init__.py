@@ -27,6 +27,10 @@ Independent cross-checks (plain C in ``oracle.c``, loaded with ctypes):
   * :func:`hopcroft`, :func:`hk_equivalent`, :func:`shortest_cex`,
     :func:`pair_table`; plus :func:`word_enumeration` in pure Python.
 
+CPU baseline (plain C in ``moore.c``): :func:`moore_c`, Moore refinement with
+hash partitions and exact signature comparison, on one thread or with OpenMP
+on all host cores (bench.py times it; tests pin it to :func:`moore`).
+
 Readings of the paper where it is silent or inconsistent (also listed in the
 design notes):
   * Round counts: ``rounds_changed`` counts rounds whose block count grew;
@@ -56,11 +60,17 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (plain gcc, no GPU)."""
-    src = os.path.join(_HERE, "oracle.c")
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+    """Compile oracle.c and moore.c into liboracle.so next to them (plain gcc,
+    with OpenMP when the compiler has it; no GPU)."""
+    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "moore.c")]
+    if force or not os.path.exists(_LIB_PATH) or \
+            os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(f) for f in srcs):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, src])
+        base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:] + srcs, stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:   # no OpenMP: the single-threaded build
+            subprocess.check_call(base + srcs)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -81,6 +91,10 @@ def _load():
         lib.oracle_hk_equivalent.restype = ctypes.c_int
         lib.oracle_shortest_cex.argtypes = [u32, u32, P32, P8, u32, u32, P32, P8, u32]
         lib.oracle_shortest_cex.restype = ctypes.c_int64
+        lib.oracle_moore_c.argtypes = [u32, u32, P32, P8, ctypes.c_int, P32, P32, P32, P32]
+        lib.oracle_moore_c.restype = ctypes.c_int
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -524,6 +538,27 @@ def product_explore(dA, accA, sA, dB, accB, sB, inclusion: bool = False) -> Prod
 # ----------------------------------------------------------------------------
 # Independent cross-checks
 # ----------------------------------------------------------------------------
+
+def moore_c(delta, accept, threads: int = 1) -> "RefineResult":
+    """Moore refinement in plain C (moore.c): the same partition and round
+    counts as :func:`moore`, for the CPU baseline.  threads = 1: one thread;
+    0: all host cores (OpenMP); else that many."""
+    delta, accept = _prep(delta, accept)
+    k, n = delta.shape
+    out = np.empty(n, dtype=np.uint32)
+    ch, ex, nb = ctypes.c_uint32(0), ctypes.c_uint32(0), ctypes.c_uint32(0)
+    rc = _load().oracle_moore_c(n, k, _p32(delta), _p8(accept), int(threads), _p32(out), ctypes.byref(ch),
+                                ctypes.byref(ex), ctypes.byref(nb))
+    if rc != 0:
+        raise RuntimeError(f"oracle_moore_c failed: {rc}")
+    res = RefineResult(out, int(nb.value), int(ch.value), int(ex.value), [])
+    return res
+
+
+def host_threads() -> int:
+    """Threads moore_c uses with threads = 0 (the host cores OpenMP sees)."""
+    return int(_load().oracle_threads())
+
 
 def hopcroft(delta, accept) -> np.ndarray:
     """Hopcroft's n log n coarsest partition (C), canonical numbering."""

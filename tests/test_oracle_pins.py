@@ -661,3 +661,44 @@ def test_pins_catch_trans_label_from_wrong_side(monkeypatch):
     except IndexError:          # a state Apart from itself: no representative
         return
     assert not np.array_equal(r.block, h) or r.apart.diagonal().any() or not np.array_equal(r.apart, r.apart.T)
+
+
+# ---------------------------------------------------------------- the C Moore refinement (CPU baseline)
+
+def _moore_c_cases():
+    yield dfagen.random_dfa(1, 2, 0.5, 1)
+    yield dfagen.random_dfa(7, 0, 0.5, 2)
+    yield dfagen.random_dfa(5000, 3, 0.0, 3)
+    yield dfagen.random_dfa(5000, 3, 1.0, 4)
+    yield dfagen.random_dfa(10_000, 2, 0.5, 1)
+    yield dfagen.random_dfa(30_001, 5, 0.3, 6)
+    yield dfagen.fibonacci_dfa(12)
+    yield dfagen.bit_splitter(10)
+    yield dfagen.chain_dfa(300)
+    yield dfagen.cycle_dfa(14)
+    yield dfagen.planted_redundancy(dfagen.random_dfa(2000, 3, 0.5, 61), 6, 2)[0]
+    yield dfagen.DFA(dfagen.bounded(9, 91, 3 * 20_000, 5).reshape(3, 20_000),
+                     dfagen.bernoulli(9, 92, 20_000, 0.5), 0)
+
+
+@pytest.mark.parametrize("idx", range(12))
+@pytest.mark.parametrize("threads", [1, 0])
+def test_moore_c_equals_moore_and_hopcroft(idx, threads):
+    """The C refinement (one thread, and OpenMP on all host cores) reaches the
+    definition-level oracle's partition with the same round counts, and
+    Hopcroft's partition."""
+    A = list(_moore_c_cases())[idx]
+    ref = oracle.moore(A.delta, A.accept)
+    got = oracle.moore_c(A.delta, A.accept, threads=threads)
+    assert np.array_equal(got.block, ref.block)
+    assert (got.num_blocks, got.rounds_changed, got.rounds_executed) == \
+        (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
+    assert np.array_equal(got.block, oracle.hopcroft(A.delta, A.accept))
+
+
+def test_moore_c_rejects_bad_targets():
+    A = dfagen.random_dfa(100, 2, 0.5, 3)
+    bad = A.delta.copy()
+    bad[1][7] = 100
+    with pytest.raises((RuntimeError, ValueError)):
+        oracle.moore_c(bad, A.accept)
