@@ -49,6 +49,8 @@ def parse():
                     help="profiling cases: 2^lg states instead of 2^24 (same k, seed and acceptance)")
     ap.add_argument("--stop-discrete", action="store_true",
                     help="profiling cases: time the call with DFA_FLAG_STOP_DISCRETE")
+    ap.add_argument("--bucketed", action="store_true",
+                    help="profiling cases: time the call with DFA_FLAG_BUCKETED (the bucketed gather)")
     ap.add_argument("--case", default="headline", choices=["headline", "batch", "serve"],
                     help="batch: time only the packed batched call on --batch-dfas DFAs of the batch recipe")
     ap.add_argument("--batch-dfas", type=int, default=4096)
@@ -609,7 +611,8 @@ def main():
     d_acc = torch.from_numpy(A.accept).cuda()
     out = torch.empty(n, dtype=torch.int32, device="cuda")
     dd, keep = g.make_dfa(d_delta, d_acc)
-    opts = g.make_opts("moore", flags=g.DFA_FLAG_STOP_DISCRETE if args.stop_discrete else 0)
+    opts = g.make_opts("moore", flags=(g.DFA_FLAG_STOP_DISCRETE if args.stop_discrete else 0) |
+                       (g.DFA_FLAG_BUCKETED if args.bucketed else 0))
     ws_bytes = g.dfa_workspace_size(dd, opts)
     ws = g._workspace(ws_bytes)
     stream = torch.cuda.current_stream()
@@ -668,7 +671,7 @@ def main():
                 "kernel_ms_device_clock": statistics.mean(dev_ns) * 1e-6,
                 "kernel_ms_source": "CUDA events around each launch on its stream"}
     prof = os.path.join(ROOT, "profiles", "moore_kernel_traffic_random_n2p24_k4.txt")
-    if os.path.exists(prof) and args.lg == 24 and not args.stop_discrete:
+    if os.path.exists(prof) and args.lg == 24 and not args.stop_discrete and not args.bucketed:
         fields = {}
         with open(prof) as f:
             for line in f:
@@ -774,6 +777,7 @@ def main():
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": dict(WORKLOAD, algo="moore (signature refinement)", rounds=rounds[-1],
                                **({"flags": "DFA_FLAG_STOP_DISCRETE"} if args.stop_discrete else {}),
+                               **({"gather": "bucketed (DFA_FLAG_BUCKETED)"} if args.bucketed else {}),
                                l2="inputs larger than L2 (delta 256 MiB)",
                                parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps,
