@@ -341,10 +341,12 @@ int dfa_serve_destroy(dfa_server *s);
  *  - delta, accept and block_out must be device pointers (else DFA_EINVAL).
  *  - The first call on a device looks the array's device address up.
  *  - Synchronous: the call waits for `stream` before it returns (it reads the
- *    round counts back), so it must not be called while `stream` is being
- *    captured into a CUDA graph.
- *  - All calls share the array: calls that overlap on the GPU race, so
- *    serialise them.  Each call clears what it needs; nothing carries over.
+ *    round counts back).  On a stream that is being captured into a CUDA
+ *    graph it enqueues nothing and returns DFA_EINVAL.
+ *  - All calls on a device share the array, so a call holds a per-device lock
+ *    until its stream has drained: calls from several host threads or on
+ *    several streams run one after another.  Each call clears what it needs;
+ *    nothing carries over.
  *  - Calls no cudaMalloc, cudaFree or allocating library routine. */
 #define DFA_NOALLOC_MAX_STATES 65536u
 int dfa_minimise_noalloc(const dfa_t *dfa, const dfa_opts *opts, uint32_t *block_out, dfa_result *res,

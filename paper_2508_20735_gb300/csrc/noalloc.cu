@@ -14,11 +14,12 @@
 // reach host memory, silently touch the wrong memory).  The device address is
 // looked up once per device with cudaGetSymbolAddress, with that device
 // current, on the first call made on it.  Every call waits for its stream (it
-// reads the round counts back), so no call may be made while that stream is
-// being captured.  Calls share the one array and leave their contents in it;
-// everything a call needs zeroed is cleared by the call itself.  Calls whose
-// work overlaps on the GPU (different streams, or another host thread) race on
-// the array: serialise them.
+// reads the round counts back), so a call on a stream that is being captured
+// is refused before anything is enqueued.  Calls on one device share the one
+// array: each holds that device's lock from its launch until its stream has
+// drained, so calls from several host threads or on several streams run one
+// after another instead of racing.  Everything a call needs zeroed is cleared
+// by the call itself.
 #include <mutex>
 
 #include "api_util.h"
@@ -36,17 +37,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 static constexpr int kMaxDevices = 64;
 static std::mutex g_noalloc_mu;
-static char *g_noalloc_ptr[kMaxDevices];   // device address per device, filled on first use
+static char *g_noalloc_ptr[kMaxDevices];          // device address per device, filled on first use
+static std::mutex g_noalloc_call_mu[kMaxDevices];   // held by a call for its whole run on that device
 
-static int noalloc_scratch(char **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return fail(DFA_EINVAL, "device %d beyond %d", dev, kMaxDevices);
+static int noalloc_scratch(int dev, char **out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // with `dev` current
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // with `dev` current
     if (e != cudaSuccess || p == nullptr) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
     g_noalloc_ptr[dev] = static_cast<char *>(p);
   }
@@ -60,6 +58,7 @@ using namespace dfa;
 
 extern "C" int dfa_minimise_noalloc(const dfa_t *d, const dfa_opts *opts, uint32_t *block_out, dfa_result *res,
                                     void *stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int rc = check_dfa(d, "dfa");
   if (rc != DFA_OK) return rc;
   if (d->n > DFA_NOALLOC_MAX_STATES)
@@ -73,10 +72,19 @@ extern "C" int dfa_minimise_noalloc(const dfa_t *d, const dfa_opts *opts, uint32
   const MooreLayout L = moore_layout(d->n, d->k, false, false, false);
   if (L.total > kNoallocScratchBytes)
     return fail(DFA_EINVAL, "scratch of %zu bytes exceeds the fixed %zu", L.total, kNoallocScratchBytes);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t ec = cudaStreamIsCapturing(st, &cs);
+  if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(DFA_EINVAL, "dfa_minimise_noalloc waits for its stream and cannot be captured into a graph");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(DFA_EINVAL, "device %d beyond %d", dev, kMaxDevices);
   char *ws = nullptr;
-  rc = noalloc_scratch(&ws);
+  rc = noalloc_scratch(dev, &ws);
   if (rc != DFA_OK) return rc;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> busy(g_noalloc_call_mu[dev]);
   const uint32_t vec = pick_vec(d->n, d->k, d->delta, d->accept, o.schedule);
   Ctrl c{};
   // run_moore clears the control block; the kernel clears its table and scratch.

@@ -6,7 +6,9 @@ cudaMalloc because it can synchronise the device.  This test calls the
 no-allocation entry point through the C ABI twice in a row (the second call on
 a smaller DFA, after the first has left its data in the shared scratch) and
 checks each result against dfa_minimise, bit for bit, and that sizes beyond
-the fixed scratch are rejected with a clear error.
+the fixed scratch are rejected with a clear error; concurrent calls from two
+host threads serialise on the shared scratch, and a call under stream capture
+is refused.
 
 The file is named to be collected last.
 """
@@ -91,3 +93,62 @@ def test_noalloc_rejects_too_many_states(g):
     st, res, _ = _noalloc(g, A)
     assert st == g.DFA_EINVAL
     assert "at most 65536 states" in g.last_error()
+
+
+def test_noalloc_concurrent_threads_on_two_streams(g):
+    """Two host threads, each on its own stream, call the no-allocation entry
+    point in a loop on different DFAs.  The calls share one scratch array; the
+    per-device lock makes them run one after another, so every result equals
+    the oracle's."""
+    import threading
+    import torch
+    import oracle
+    As = []
+    for i in range(2):
+        base = dfagen.random_dfa(300 + 200 * i, 3, 0.5, 80 + i)
+        A, _ = dfagen.planted_redundancy(base, 4 + i, 90 + i)
+        As.append(A)
+    refs = [oracle.moore(A.delta, A.accept) for A in As]
+    results = [[], []]
+
+    def work(i):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            for _ in range(6):
+                st, res, got = _noalloc(g, As[i])
+                results[i].append((st, res.num_blocks, res.rounds_executed, got))
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for i in range(2):
+        assert len(results[i]) == 6
+        for st, nb, rx, got in results[i]:
+            assert st == g.DFA_OK
+            assert np.array_equal(got, refs[i].block)
+            assert (nb, rx) == (refs[i].num_blocks, refs[i].rounds_executed)
+
+
+def test_noalloc_refuses_graph_capture(g):
+    """On a stream that is being captured the call enqueues nothing and
+    returns DFA_EINVAL; the next ordinary call still works."""
+    import torch
+    A = dfagen.random_dfa(1_000, 2, 0.5, 78)
+    d = torch.from_numpy(np.ascontiguousarray(A.delta).view(np.int32)).cuda()
+    a = torch.from_numpy(np.ascontiguousarray(A.accept)).cuda()
+    out = torch.full((A.n,), -1, dtype=torch.int32, device="cuda")
+    dd, keep = g.make_dfa(d, a)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        st, _ = g.dfa_minimise_noalloc(dd, None, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert st == g.DFA_EINVAL
+    assert "captured" in g.last_error()
+    assert int((out == -1).sum()) == A.n     # nothing ran
+    st, res, got = _noalloc(g, A)
+    assert st == g.DFA_OK, g.last_error()
+    ref_res, ref = _reference(g, A)
+    assert np.array_equal(got, ref)
