@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -358,7 +359,9 @@ def extras(g):
             row[algo] = {"device_ms": r.device_ns / 1e6, "rounds": r.rounds_executed, "blocks": r.num_blocks}
         cm[name] = row
     out["closure_moore_vs_trans"] = cm
-    # batch of 4,096 DFAs: one launch vs one dfa_minimise per DFA
+    # batch of 4,096 DFAs: one launch vs one dfa_minimise per DFA; the autotuner
+    # writes to a fresh cache file, so that its choice is measured in this run
+    os.environ["DFA_AUTOTUNE_CACHE"] = os.path.join(tempfile.mkdtemp(prefix="dfa_tune_"), "autotune.json")
     dfas = dfagen.batch_dfas(4096, 64, 65_536, 2, 8, 0.3, 4)
     items = [_dev(X) for X in dfas]
     pn, pk, pd, pa = g.pack_batch([(X.delta, X.accept) for X in dfas])   # resident on the device, packed
@@ -384,9 +387,34 @@ def extras(g):
                          "batched_device_ms": dev_ms, "list_form_ms": tl * 1e3,
                          "form": "packed (dfa_minimise_batch_packed); list_form_ms: one dfa_t per DFA",
                          "cpu_oracle_dfas_per_s": {"1_core": c1, f"{cores}_cores": cN},
-                         "cpu_sample": "oracle/moore.c, one DFA per thread, the first 512 DFAs of the recipe"}
+                         "cpu_sample": "oracle/moore.c, one DFA per thread, the first 512 DFAs of the recipe",
+                         "autotune": autotune_record(), "graph": dict(zip(("instantiations", "updates"),
+                                                                          g.batch_graph_stats()))}
     out["serve_equiv"] = serve_study(g, pairs=1000, nreq=10_000)
     return out
+
+
+def schedule_name(s):
+    """The batch kernel's schedule s: states per lane and states per tile."""
+    return f"{1 + (s & 1)} state(s) per lane, tile {256 >> (s >> 1)}"
+
+
+def autotune_record():
+    """The batch autotuner's entries in its cache file: the chosen schedule, every
+    schedule's device time, and the margin of the choice over the runner-up."""
+    path = os.environ.get("DFA_AUTOTUNE_CACHE")
+    if not path or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        cache = json.load(f)
+    rec = {}
+    for key, entry in cache.items():
+        choice, ns = entry[0], entry[1:]
+        ranked = sorted(t for t in ns if t > 0)
+        rec[key] = {"choice": schedule_name(choice),
+                    "device_ms": {schedule_name(s): t / 1e6 for s, t in enumerate(ns)},
+                    "margin_vs_runner_up": (ranked[1] / ranked[0] - 1.0) if len(ranked) > 1 else None}
+    return rec
 
 
 def _best_of(fn, reps):
@@ -514,6 +542,8 @@ def run_batch_case(args, local):
     import paper_2508_20735_gb300 as g
     torch.cuda.set_device(local)
     g.build()
+    if args.schedule < 0:
+        os.environ["DFA_AUTOTUNE_CACHE"] = os.path.join(tempfile.mkdtemp(prefix="dfa_tune_"), "autotune.json")
     dfas = dfagen.batch_dfas(args.batch_dfas, 64, 65_536, 2, 8, 0.3, 4)
     pn, pk, pd, pa = g.pack_batch([(X.delta, X.accept) for X in dfas])
     out = torch.empty(int(pn.sum()), dtype=torch.int32, device="cuda")
@@ -531,7 +561,10 @@ def run_batch_case(args, local):
                       "unit": "DFAs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": el * 1e3 / args.steps, "device_ms": statistics.median(dev) / 1e6,
                       "higher_is_better": True, "dtype": "u32", "data": "synthetic",
-                      "config": {"workload": f"batch_{args.batch_dfas}_dfas", "states": int(pn.sum())},
+                      "config": {"workload": f"batch_{args.batch_dfas}_dfas", "states": int(pn.sum()),
+                                 "schedule": "autotuned" if args.schedule < 0 else schedule_name(args.schedule)},
+                      "autotune": autotune_record() if args.schedule < 0 else None,
+                      "graph": dict(zip(("instantiations", "updates"), g.batch_graph_stats())),
                       "clocks": clk.summary(), "gpu_launches": args.steps}), flush=True)
 
 

@@ -72,6 +72,7 @@ _SIGS = [
                                                    POINTER(DfaOpts)]),
     ("dfa_minimise_batch_packed", c_int, [c_uint32, c_void_p, c_void_p, c_void_p, c_void_p, POINTER(DfaOpts),
                                           c_void_p, POINTER(DfaResult), c_void_p, c_size_t, c_void_p]),
+    ("dfa_batch_graph_stats", c_int, [POINTER(c_uint64), POINTER(c_uint64)]),
     ("dfa_equivalent_workspace_size", c_size_t, [POINTER(DfaT), POINTER(DfaT), POINTER(DfaOpts)]),
     ("dfa_equivalent", c_int, [POINTER(DfaT), POINTER(DfaT), POINTER(DfaOpts), POINTER(c_int), POINTER(DfaResult),
                                c_void_p, c_size_t, c_void_p]),
@@ -214,6 +215,13 @@ def dfa_minimise_noalloc(dfa: DfaT, opts: DfaOpts | None, block_out_ptr: int,
     st = lib().dfa_minimise_noalloc(ctypes.byref(dfa), ctypes.byref(opts) if opts else None, block_out_ptr,
                                     ctypes.byref(res), stream)
     return st, res
+
+
+def batch_graph_stats() -> tuple[int, int]:
+    """(instantiations, updates) of the batch calls' CUDA graph in this process."""
+    i, u = c_uint64(0), c_uint64(0)
+    lib().dfa_batch_graph_stats(ctypes.byref(i), ctypes.byref(u))
+    return int(i.value), int(u.value)
 
 
 def dfa_equivalent_workspace_size(a: DfaT, b: DfaT, opts: DfaOpts | None = None) -> int:

@@ -6,10 +6,11 @@
 // [state_off_i, state_off_i + n_i) of the label arrays and its own region of
 // 2^ceil(log2(2 n_i)) slots of the renumbering table, so keys of different DFAs
 // never meet and labels stay narrow (a DFA with 65,536 states packs 17-bit
-// components).  Work is cut into tiles of at most kTile states that never
-// cross a DFA boundary (listed on the device at the start of the launch from
-// each DFA's first tile number); warps take tiles grid-stride and skip the
-// tiles of DFAs that have already converged.
+// components).  Work is cut into tiles of at most `tile` states (64, 128 or
+// 256, part of the schedule) that never cross a DFA boundary (listed on the
+// device at the start of the launch from each DFA's first tile number); warps
+// take tiles grid-stride and skip the tiles of DFAs that have already
+// converged.
 //
 // Rounds.  Every pass packs each active state's signature into a key of its
 // own DFA's width and inserts it into its DFA's table region; a new slot counts
@@ -19,6 +20,7 @@
 // The launch ends when no DFA is active; then the final labels are gathered,
 // numbered canonically across the batch and rebased per DFA.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -34,8 +36,19 @@
 namespace dfa {
 
 static constexpr int kBatchThreads = 512;
-static constexpr uint32_t kTile = 256;
 static constexpr size_t kMaxGridB = 8192;
+
+// Schedules of the batch kernel, chosen per call (opts.schedule) or by the
+// autotuner: states per lane within a tile pass (1, two blocks of 512 threads
+// per SM; or 2, one block per SM with room for twice the keys) and states per
+// tile (256, 128 or 64: smaller tiles balance the passes between grid barriers
+// better and cost more per-tile bookkeeping).  Schedule s takes 1 + (s & 1)
+// states per lane and 256 >> (s >> 1) states per tile.
+static constexpr int kBatchSchedules = 6;
+struct BatchSchedule {
+  uint32_t vec, tile;
+};
+static inline BatchSchedule batch_schedule(int s) { return BatchSchedule{1u + (uint32_t)(s & 1), 256u >> (s >> 1)}; }
 
 struct SegInfo {
   const uint32_t *delta;   // device
@@ -91,6 +104,7 @@ struct BatchArgs {
   uint32_t ebits, max_stages, max_rounds;
   uint32_t stop_discrete;  // 1: a DFA whose round leaves n blocks stops (no confirming round)
   uint32_t vec;            // states per lane within a tile pass: 1 or 2
+  uint32_t tile;           // states per tile: 64, 128 or 256
   unsigned long long timeout_ns, barrier_ns;
 };
 
@@ -546,8 +560,8 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
   for (uint32_t i = gwarp; i < A.nsegs; i += nwarps) {
     const uint32_t t0 = A.tile_off[i], nt = A.tile_off[i + 1] - t0, n = A.segs[i].n;
     for (uint32_t j = lane; j < nt; j += 32) {
-      const uint32_t start = j * kTile;
-      A.tiles[t0 + j] = Tile{i, start, n - start < kTile ? n - start : kTile};
+      const uint32_t start = j * A.tile;
+      A.tiles[t0 + j] = Tile{i, start, n - start < A.tile ? n - start : A.tile};
     }
   }
   bool ok = grid_sync(C, A.barrier_ns);
@@ -823,7 +837,7 @@ static BatchInputs classify_inputs(const dfa_t *dfas, uint32_t count) {
   return in;
 }
 
-static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchInputs &in,
+static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchInputs &in, uint32_t tile,
                                 std::vector<SegInfo> *segs_out, std::vector<uint32_t> *tile_off_out,
                                 std::vector<size_t> *stage_off) {
   BatchLayout L{};
@@ -860,7 +874,7 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchIn
       }
     }
     if (tile_off_out) tile_off_out->push_back(ntiles);
-    ntiles += (d.n + kTile - 1) / kTile;
+    ntiles += (d.n + tile - 1) / tile;
     // host-resident arrays are staged into the workspace
     const bool hd = in.host[2 * i], ha = in.host[2 * i + 1];
     const size_t db = (size_t)d.k * d.n * 4, ab = d.n;
@@ -909,7 +923,7 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchIn
   L.seen3 = take(((size_t)1 << L.mbits) / 16);
   L.seen4 = take(((size_t)1 << L.mbits) / 16);
   L.rep = take(sl * 8);
-  L.list_entries = ((size_t)ntiles + batch_max_warps() / (kBatchThreads / 32)) * kTile;   // per block: its tiles
+  L.list_entries = ((size_t)ntiles + batch_max_warps() / (kBatchThreads / 32)) * tile;   // per block: its tiles
   L.dups = take(L.list_entries * 4);
   L.dups2 = take(L.list_entries * 4);
   L.dups3 = take(L.list_entries * 4);
@@ -954,40 +968,83 @@ static size_t batch_max_warps() {
 
 // Launches the batch kernel as a CUDA graph: the control-block reset and the
 // cooperative launch are captured on a library-owned stream (capture is not
-// allowed on the legacy default stream) and the graph runs on `st`.
+// allowed on the legacy default stream) and the graph runs on `st`.  The
+// instantiated graph is kept per host thread and per kernel variant: a later
+// call captures its own two nodes (new pointers, new grid) and moves them into
+// the kept executable with cudaGraphExecUpdate, which costs a fraction of a new
+// instantiation; only when the update is refused is the graph instantiated
+// again.  An update affects later launches only, and launches of one
+// executable run in order, so a call never changes a launch still in flight.
+struct GraphCache {
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};   // by states per lane - 1
+  ~GraphCache() {   // at thread exit; errors are ignored (the runtime may be gone at process exit)
+    for (cudaGraphExec_t &x : exec)
+      if (x) cudaGraphExecDestroy(x);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+static thread_local GraphCache g_graphs;
+static std::atomic<uint64_t> g_graph_instantiations{0}, g_graph_updates{0};
+
 static cudaError_t launch_batch_graph(const BatchArgs &a, int grid, cudaStream_t st) {
-  static thread_local cudaStream_t cap = nullptr;
+  GraphCache &G = g_graphs;
   cudaError_t e;
-  if (!cap && (e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if (!G.cap && (e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
   cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   BatchArgs copy = a;
   void *params[] = {&copy};
-  cudaError_t le = cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), cap);
+  cudaError_t le = cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), G.cap);
   if (le == cudaSuccess)
-    le = cudaLaunchCooperativeKernel(batch_kernel_for(a.vec), dim3(grid), dim3(kBatchThreads), params, 0, cap);
-  e = cudaStreamEndCapture(cap, &graph);
+    le = cudaLaunchCooperativeKernel(batch_kernel_for(a.vec), dim3(grid), dim3(kBatchThreads), params, 0, G.cap);
+  e = cudaStreamEndCapture(G.cap, &graph);
   if (le != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     return le;
   }
   if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(&exec, graph, 0);
-  if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
-  if (exec) cudaGraphExecDestroy(exec);
+  cudaGraphExec_t &exec = G.exec[a.vec == 2 ? 1 : 0];
+  bool updated = false;
+  if (exec) {
+    cudaGraphExecUpdateResultInfo info{};
+    updated = cudaGraphExecUpdate(exec, graph, &info) == cudaSuccess;
+    if (!updated) {
+      cudaGetLastError();   // a refused update is not an error of this call
+      cudaGraphExecDestroy(exec);
+      exec = nullptr;
+    }
+  }
+  if (!exec) {
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+      exec = nullptr;
+      cudaGraphDestroy(graph);
+      return e;
+    }
+    g_graph_instantiations.fetch_add(1, std::memory_order_relaxed);
+  } else if (updated) {
+    g_graph_updates.fetch_add(1, std::memory_order_relaxed);
+  }
   cudaGraphDestroy(graph);
-  return e;
+  return cudaGraphLaunch(exec, st);
 }
 
 // ------------------------------------------------------------------ autotuner
-// Schedules: 0 = one state per lane, 1 = two states per lane.  With
-// opts.schedule = -1 the first call for a (batch size bucket, letter bucket,
-// GPU) key times both on the batch itself and remembers the faster, in memory
-// and in a JSON file ($DFA_AUTOTUNE_CACHE, default ~/.cache/dfa_gb300_autotune.json).
+// With opts.schedule = -1 the first call for a (GPU, total-states bucket,
+// batch-size bucket, largest k) key runs the batch once under every schedule,
+// keeps the fastest by device time, and remembers the choice together with
+// every schedule's time, in memory and in a JSON file ($DFA_AUTOTUNE_CACHE,
+// default ~/.cache/dfa_gb300_autotune.json), one entry per line:
+//   "batch|<GPU>|states2^a|dfas2^b|kmaxc": [choice, ns_0, ns_1, ..., ns_5]
+// Later calls with the same key run the remembered schedule directly.
+struct TuneEntry {
+  int choice = -1;
+  std::vector<uint64_t> ns;   // device time per schedule (0 = not measured)
+};
 static std::mutex g_tune_mu;
-static std::map<std::string, int> g_tune;
+static std::map<std::string, TuneEntry> g_tune;
 static bool g_tune_loaded = false;
 
 static std::string tune_path() {
@@ -1003,11 +1060,25 @@ static void tune_load() {
   FILE *f = fopen(tune_path().c_str(), "r");
   if (!f) return;
   char key[256];
-  int val;
-  // format: {"key": value, ...} one entry per line
-  char line[512];
+  char line[1024];
   while (fgets(line, sizeof line, f)) {
-    if (sscanf(line, " \"%255[^\"]\" : %d", key, &val) == 2) g_tune[key] = val;
+    int used = 0;
+    if (sscanf(line, " \"%255[^\"]\" : [%n", key, &used) != 1 || used == 0) continue;
+    TuneEntry e;
+    const char *c = line + used;
+    char *end = nullptr;
+    const long ch = strtol(c, &end, 10);
+    if (end == c || ch < 0 || ch >= kBatchSchedules) continue;
+    e.choice = (int)ch;
+    c = end;
+    while (*c == ',' || *c == ' ') {
+      ++c;
+      const unsigned long long v = strtoull(c, &end, 10);
+      if (end == c) break;
+      e.ns.push_back(v);
+      c = end;
+    }
+    g_tune[key] = e;
   }
   fclose(f);
 }
@@ -1020,7 +1091,11 @@ static void tune_save() {
   if (!f) return;
   fprintf(f, "{\n");
   size_t i = 0;
-  for (auto &kv : g_tune) fprintf(f, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++i < g_tune.size() ? "," : "");
+  for (auto &kv : g_tune) {
+    fprintf(f, "  \"%s\": [%d", kv.first.c_str(), kv.second.choice);
+    for (uint64_t v : kv.second.ns) fprintf(f, ", %llu", (unsigned long long)v);
+    fprintf(f, "]%s\n", ++i < g_tune.size() ? "," : "");
+  }
   fprintf(f, "}\n");
   fclose(f);
 }
@@ -1070,18 +1145,23 @@ static size_t batch_workspace_impl(const dfa_t *dfas, uint32_t count, const Batc
   uint64_t total;
   uint32_t kmax;
   if (check_batch(dfas, count, &total, &kmax) != DFA_OK) return 0;
-  const BatchLayout L = batch_layout(dfas, count, in, nullptr, nullptr, nullptr);
-  if (L.total_slots > 0xFFFFFFFFull) return 0;
-  return L.total;
+  size_t most = 0;
+  for (int sc = 0; sc < kBatchSchedules; ++sc) {   // the workspace serves every schedule
+    const BatchLayout L = batch_layout(dfas, count, in, batch_schedule(sc).tile, nullptr, nullptr, nullptr);
+    if (L.total_slots > 0xFFFFFFFFull) return 0;
+    most = std::max(most, L.total);
+  }
+  return most;
 }
 
 static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, const dfa_opts &o,
-                     uint32_t *block_out, dfa_result *res, char *ws, size_t ws_bytes, cudaStream_t st, uint32_t vec,
+                     uint32_t *block_out, dfa_result *res, char *ws, size_t ws_bytes, cudaStream_t st, int schedule,
                      uint64_t *device_ns) {
+  const uint32_t vec = batch_schedule(schedule).vec, tile = batch_schedule(schedule).tile;
   std::vector<SegInfo> segs;
   std::vector<uint32_t> tile_off;
   std::vector<size_t> stage_off;
-  const BatchLayout L = batch_layout(dfas, count, in, &segs, &tile_off, &stage_off);
+  const BatchLayout L = batch_layout(dfas, count, in, tile, &segs, &tile_off, &stage_off);
   if (L.total_slots > 0xFFFFFFFFull) return fail(DFA_EINVAL, "batch too large for 32-bit labels");
   if (ws_bytes < L.total) return fail(DFA_EINVAL, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
   cudaError_t e;
@@ -1172,6 +1252,7 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
   a.max_rounds = o.max_rounds;
   a.stop_discrete = (o.flags & DFA_FLAG_STOP_DISCRETE) ? 1u : 0u;
   a.vec = vec;
+  a.tile = tile;
   a.timeout_ns = o.timeout_ns;
   a.barrier_ns = o.timeout_ns < 5000000000ull ? o.timeout_ns : 5000000000ull;
   int dev = 0, sms = 0, per_sm = 0;
@@ -1186,7 +1267,7 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
   // list capacity per block: the states of the block's tiles (tiles t = block + j * grid)
   if ((size_t)grid * (kBatchThreads / 32) > batch_max_warps())
     return fail(DFA_ECUDA, "grid larger than the workspace was sized for");
-  a.dup_cap = (uint32_t)(((size_t)L.ntiles + grid - 1) / grid * kTile);
+  a.dup_cap = (uint32_t)(((size_t)L.ntiles + grid - 1) / grid * tile);
   e = launch_batch_graph(a, grid, st);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch of the batch kernel");
   Ctrl c{};
@@ -1231,8 +1312,8 @@ static int minimise_batch_impl(const dfa_t *dfas, uint32_t count, const BatchInp
   if (o.algo != DFA_ALGO_MOORE) return fail(DFA_EINVAL, "batches use signature refinement (algo 0)");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char *ws = static_cast<char *>(workspace);
-  if (o.schedule == 0 || o.schedule == 1)
-    return run_batch(dfas, count, in, o, block_out, res, ws, ws_bytes, st, o.schedule == 1 ? 2u : 1u, nullptr);
+  if (o.schedule >= kBatchSchedules) return fail(DFA_EINVAL, "batch schedule %d beyond %d", o.schedule, kBatchSchedules - 1);
+  if (o.schedule >= 0) return run_batch(dfas, count, in, o, block_out, res, ws, ws_bytes, st, o.schedule, nullptr);
   // autotune
   const std::string key = tune_key(total, count, kmax);
   int choice = -1;
@@ -1240,24 +1321,28 @@ static int minimise_batch_impl(const dfa_t *dfas, uint32_t count, const BatchInp
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_load();
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) choice = it->second;
+    if (it != g_tune.end()) choice = it->second.choice;
   }
-  if (choice != 0 && choice != 1) {
+  if (choice < 0 || choice >= kBatchSchedules) {
+    TuneEntry e;
+    e.ns.assign(kBatchSchedules, 0);
     uint64_t best = ~0ull;
-    for (int s = 0; s < 2; ++s) {
+    for (int sc = 0; sc < kBatchSchedules; ++sc) {
       uint64_t ns = 0;
-      const int rc = run_batch(dfas, count, in, o, block_out, res, ws, ws_bytes, st, s == 1 ? 2u : 1u, &ns);
+      const int rc = run_batch(dfas, count, in, o, block_out, res, ws, ws_bytes, st, sc, &ns);
       if (rc != DFA_OK && rc != DFA_EMAXROUNDS) return rc;
+      e.ns[sc] = ns;
       if (ns < best) {
         best = ns;
-        choice = s;
+        choice = sc;
       }
     }
+    e.choice = choice;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[key] = choice;
+    g_tune[key] = e;
     tune_save();
   }
-  return run_batch(dfas, count, in, o, block_out, res, ws, ws_bytes, st, choice == 1 ? 2u : 1u, nullptr);
+  return run_batch(dfas, count, in, o, block_out, res, ws, ws_bytes, st, choice, nullptr);
 }
 
 // dfa_t entries of a packed batch (pieces of the two buffers, in DFA order).
@@ -1292,6 +1377,12 @@ static int packed_dfas(uint32_t count, const uint32_t *n, const uint32_t *k, con
 }
 
 extern "C" {
+
+int dfa_batch_graph_stats(uint64_t *instantiations, uint64_t *updates) {
+  if (instantiations) *instantiations = g_graph_instantiations.load(std::memory_order_relaxed);
+  if (updates) *updates = g_graph_updates.load(std::memory_order_relaxed);
+  return DFA_OK;
+}
 
 size_t dfa_batch_workspace_size(const dfa_t *dfas, uint32_t count, const dfa_opts *opts) {
   (void)opts;

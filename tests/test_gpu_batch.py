@@ -51,7 +51,7 @@ def _mixed():
     return dfas
 
 
-@pytest.mark.parametrize("schedule", [0, 1, -1])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4, 5, -1])
 def test_mixed_batch_against_oracle(g, schedule):
     dfas = _mixed()
     blocks, res = _batch(g, dfas, schedule=schedule)
@@ -62,7 +62,7 @@ def test_mixed_batch_against_oracle(g, schedule):
             (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
 
 
-@pytest.mark.parametrize("schedule", [0, -1])
+@pytest.mark.parametrize("schedule", [0, 5, -1])
 def test_mixed_batch_stop_discrete(g, schedule):
     dfas = _mixed()
     blocks, res = _batch(g, dfas, schedule=schedule, flags=g.DFA_FLAG_STOP_DISCRETE)
@@ -71,6 +71,45 @@ def test_mixed_batch_stop_discrete(g, schedule):
         assert np.array_equal(b, ref.block)
         assert (r.num_blocks, r.rounds_changed, r.rounds_executed) == \
             (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
+
+
+def test_autotuner_records_every_schedule(g):
+    """The autotuner times all six schedules once per batch shape, keeps the
+    fastest, and writes the choice and every time to its cache file."""
+    import json
+    dfas = [dfagen.random_dfa(n, k, 0.3, 950 + i) for i, (n, k) in enumerate(
+        [(3000, 3), (20_000, 5), (777, 2), (40_000, 7)])]
+    blocks, res = _batch(g, dfas, schedule=-1)
+    for A, b in zip(dfas, blocks):
+        assert np.array_equal(b, oracle.moore(A.delta, A.accept).block)
+    with open(os.environ["DFA_AUTOTUNE_CACHE"]) as f:
+        cache = json.load(f)
+    kmax = [key for key in cache if key.startswith("batch|") and key.endswith("|kmax7")]
+    assert kmax, cache
+    entry = cache[kmax[0]]
+    choice, times = entry[0], entry[1:]
+    assert len(times) == 6 and all(t > 0 for t in times)
+    assert 0 <= choice < 6 and times[choice] == min(times)
+
+
+def test_batch_schedule_out_of_range(g):
+    with pytest.raises(g.DfaError) as e:
+        _batch(g, [dfagen.random_dfa(100, 2, 0.5, 3)], schedule=6)
+    assert e.value.status == g.DFA_EINVAL
+
+
+def test_batch_graph_is_reused(g):
+    """Repeated calls in one thread update the kept graph instead of
+    instantiating a new one."""
+    dfas = _mixed()[:6]
+    _batch(g, dfas, schedule=0)
+    i0, u0 = g.batch_graph_stats()
+    for _ in range(3):
+        blocks, _ = _batch(g, dfas, schedule=0)
+    i1, u1 = g.batch_graph_stats()
+    assert i1 == i0 and u1 - u0 == 3
+    for A, b in zip(dfas, blocks):
+        assert np.array_equal(b, oracle.moore(A.delta, A.accept).block)
 
 
 def test_batch_equals_alone_and_host_inputs(g):
