@@ -250,18 +250,21 @@ def extras(g):
     out = {}
     import oracle
     cores = oracle.host_threads()
-    # random DFA, n = 10,000, k = 2 (small: the single-block kernel), against the cooperative kernel and the C oracle
+    # random DFA, n = 10,000, k = 2 (small: the cluster kernel), against the single-block and
+    # cooperative kernels and the C oracle
     A = dfagen.random_dfa(10_000, 2, 0.5, 1)
     d, a = _dev(A)
     res = g.minimise(d, a)[1]
-    dev, coop = [], []
+    dev, one, coop = [], [], []
     for _ in range(20):
         dev.append(g.minimise(d, a)[1].device_ns)
+        one.append(g.minimise(d, a, flags=g.DFA_FLAG_ONE_BLOCK)[1].device_ns)
         coop.append(g.minimise(d, a, schedule=1)[1].device_ns)
     cpu1 = _best_of(lambda: oracle.moore_c(A.delta, A.accept, threads=1), 5)
     cpuN = _best_of(lambda: oracle.moore_c(A.delta, A.accept, threads=0), 5)
     out["random_n1e4_k2"] = {"device_us": statistics.median(dev) / 1e3, "rounds": res.rounds_executed,
-                             "kernel": "single thread block (n <= 16,384)",
+                             "kernel": "one thread-block cluster (n <= 16,384)",
+                             "single_block_kernel_device_us": statistics.median(one) / 1e3,
                              "cooperative_kernel_device_us": statistics.median(coop) / 1e3,
                              "transitions_per_s": A.n * A.k * res.rounds_executed / (statistics.median(dev) * 1e-9),
                              "cpu_oracle_us": {"1_core": cpu1 * 1e6, f"{cores}_cores": cpuN * 1e6}}

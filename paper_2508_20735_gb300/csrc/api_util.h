@@ -51,12 +51,18 @@ int enqueue_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t
                   uint32_t vec_ok, bool independent_letters = true);
 int status_from_ctrl(const Ctrl &c);
 
-// Signature refinement of a small DFA in one thread block (small.cu): used by
-// dfa_minimise and dfa_minimise_async when small_fits; results in *ctrl.
+// Signature refinement of a small DFA in one thread block (small.cu) or one
+// thread-block cluster (cluster.cu): used by dfa_minimise and
+// dfa_minimise_async when small_fits; results in *ctrl.
 static constexpr uint32_t kSmallMaxStates = 16384;
 bool small_fits(uint32_t n, uint32_t k, const dfa_opts &o);
 int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
                   const dfa_opts &o, cudaStream_t st);
+// The same on one thread-block cluster (cluster.cu), where the device can place
+// one and the DFA fits; enqueue_small takes it unless DFA_FLAG_ONE_BLOCK is set.
+bool cluster_fits(uint32_t n, uint32_t k, const dfa_opts &o);
+int enqueue_cluster(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
+                    const dfa_opts &o, cudaStream_t st);
 
 // naivePR / transPR (naive.cu)
 size_t naive_workspace_size(const dfa_t *d, const dfa_opts &o);

@@ -55,6 +55,27 @@ __device__ __forceinline__ unsigned long long gtimer() {
 
 // Records the end of a phase (tag < 256) in the control block; called by one
 // thread after a grid barrier, so entries are ordered in time.
+// Trace tags (Ctrl::trace): the phase that ended at the recorded time.
+enum : uint32_t {
+  kTraceStart = 1,      // set-up (clearing, staging; the bucketed kernel's sorting of δ)
+  kTraceGather = 2,     // bucketed gather of a round
+  kTraceAssemble = 3,   // bucketed filter round: signatures hashed and partitioned
+  kTraceDedup = 4,      // bucketed filter round: partitions deduplicated
+  kTraceExact = 5,      // filter round: exact inserts of the listed states
+  kTraceRound = 8,      // end of a round (| mode << 4)
+  kTraceEnd = 0xFF,     // canonical numbering done
+};
+
+// The same with the entry count and the start time kept by the caller in
+// registers (nothing loaded from memory: for kernels whose rounds last
+// microseconds).  nt starts at 0; t_start is the value stored in c->t_start.
+__device__ __forceinline__ void trace_put(Ctrl *c, uint32_t &nt, unsigned long long t_start, uint32_t tag) {
+  if (nt < kTraceLen) {
+    c->trace[nt] = ((gtimer() - t_start) << 8) | tag;
+    c->ntrace = ++nt;
+  }
+}
+
 __device__ __forceinline__ void trace_mark(Ctrl *c, uint32_t tag) {
   const uint32_t i = c->ntrace;
   if (i < kTraceLen) {
@@ -575,6 +596,90 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t *smem) {
   uint32_t total;
   (void)block_excl_scan(v, smem, &total);
   return total;
+}
+
+// ----------------------------------------------------------------- staging into shared memory
+
+// Initial labels 0/1 of all n states into lab (16-bit), and the classes seen
+// (bit 0: accepting, bit 1: rejecting).  lab is 16-byte aligned.
+__device__ __forceinline__ void stage_accept(const uint8_t *__restrict__ acc, uint32_t n, uint16_t *lab,
+                                             uint32_t *seen) {
+  const uint32_t tid = threadIdx.x, bd = blockDim.x;
+  uint32_t head = 0;
+  if ((reinterpret_cast<uintptr_t>(acc) & 15u) == 0) {
+    const uint32_t n16 = n >> 4;   // 16 states per load
+    const uint4 *a4 = reinterpret_cast<const uint4 *>(acc);
+    for (uint32_t base = 0; base < n16; base += 4u * bd) {
+      uint4 v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t i = base + j * bd + tid;
+        v[j] = i < n16 ? a4[i] : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t i = base + j * bd + tid;
+        if (i >= n16) continue;
+        const uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+        uint32_t o[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {   // bytes 2b and 2b+1 -> two halfwords
+          const uint32_t x = w[b >> 1] >> ((b & 1) * 16);
+          const uint32_t lo = (x & 0xFFu) != 0, hi = (x & 0xFF00u) != 0;
+          o[b] = lo | (hi << 16);
+          *seen |= (lo | hi ? 1u : 0u) | (!lo || !hi ? 2u : 0u);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(lab + 16u * i);
+        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+      }
+    }
+    head = n16 << 4;
+  }
+  for (uint32_t q = head + tid; q < n; q += bd) {
+    const uint32_t f = acc[q] != 0;
+    lab[q] = (uint16_t)f;
+    *seen |= f ? 1u : 2u;
+  }
+}
+
+// δ (count = k n targets) into 16-bit targets d16 (8-byte aligned); a target
+// >= n sets *bad and is stored as 0.
+__device__ __forceinline__ void stage_delta(const uint32_t *__restrict__ delta, size_t count, uint32_t n,
+                                            uint16_t *d16, uint32_t *bad) {
+  const uint32_t tid = threadIdx.x, bd = blockDim.x;
+  size_t head = 0;
+  if ((reinterpret_cast<uintptr_t>(delta) & 15u) == 0) {
+    const size_t c4 = count >> 2;   // 4 targets per load
+    const uint4 *d4 = reinterpret_cast<const uint4 *>(delta);
+    for (size_t base = 0; base < c4; base += 8u * bd) {
+      uint4 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const size_t i = base + (size_t)j * bd + tid;
+        v[j] = i < c4 ? d4[i] : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const size_t i = base + (size_t)j * bd + tid;
+        if (i >= c4) continue;
+        const uint32_t t[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+        uint32_t o[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          *bad |= t[b] >= n;
+          o[b] = t[b] < n ? t[b] : 0u;
+        }
+        *reinterpret_cast<uint2 *>(d16 + 4 * i) = make_uint2(o[0] | (o[1] << 16), o[2] | (o[3] << 16));
+      }
+    }
+    head = c4 << 2;
+  }
+  for (size_t i = head + tid; i < count; i += bd) {
+    const uint32_t d = delta[i];
+    *bad |= d >= n;
+    d16[i] = (uint16_t)(d < n ? d : 0u);
+  }
 }
 
 // Arguments of the canonical numbering that ends every refinement kernel.

@@ -1168,17 +1168,6 @@ __device__ __forceinline__ void filter_list_c(const MooreArgs &A, uint32_t *__re
 
 enum : uint32_t { MODE_DIRECT = 0, MODE_TABLE = 1, MODE_FILTER = 2 };
 
-// Trace tags (Ctrl::trace): the phase that ended at the recorded time.
-enum : uint32_t {
-  kTraceStart = 1,      // set-up (clearing; the bucketed kernel's sorting of δ)
-  kTraceGather = 2,     // bucketed gather of a round
-  kTraceAssemble = 3,   // bucketed filter round: signatures hashed and partitioned
-  kTraceDedup = 4,      // bucketed filter round: partitions deduplicated
-  kTraceExact = 5,      // filter round: exact inserts of the listed states
-  kTraceRound = 8,      // end of a round (| mode << 4)
-  kTraceEnd = 0xFF,     // canonical numbering done
-};
-
 // BUCKET: the bucketed gather (one 1024-thread block per SM with the shared
 // memory of BucketPlan::smem); rounds whose exact key needs several stages
 // keep the direct label reads.

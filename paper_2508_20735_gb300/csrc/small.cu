@@ -61,9 +61,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
   const uint32_t twords = A.wide_table ? 2u * T : T;
   uint32_t *tbl = sm;                                             // table (also the direct rounds' flags)
   unsigned long long *tbl64 = reinterpret_cast<unsigned long long *>(sm);
-  uint16_t *lab[2] = {reinterpret_cast<uint16_t *>(sm + twords),
-                      reinterpret_cast<uint16_t *>(sm + twords) + ((n + 1u) & ~1u)};
-  uint16_t *d16 = lab[1] + ((n + 1u) & ~1u);                      // k n halfwords when staged
+  // label arrays of n rounded up to 8 halfwords, so that both and d16 start on 16 bytes
+  uint16_t *const lab0 = reinterpret_cast<uint16_t *>(sm + twords), *const lab1 = lab0 + ((n + 7u) & ~7u);
+  uint16_t *d16 = lab1 + ((n + 7u) & ~7u);                      // k n halfwords when staged
   volatile uint32_t *vtbl = tbl;
   Ctrl *C = A.ctrl;
   const unsigned long long t0 = gtimer();
@@ -73,25 +73,20 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
   }
   __syncthreads();   // s_flag is clear before any thread reports into it
   // the initial partition {F, Q \ F}: labels 0/1, B_0 = the classes present
-  uint32_t seen = 0;
-  for (uint32_t q = tid; q < n; q += bd) {
-    const uint32_t f = A.accept[q] != 0;
-    lab[0][q] = (uint16_t)f;
-    seen |= f ? 1u : 2u;
-  }
-  uint32_t bad = 0;
+  // (16-byte loads where the arrays allow, several in flight per thread: the
+  // staging is latency-bound otherwise)
+  uint32_t seen = 0, bad = 0;
+  stage_accept(A.accept, n, lab0, &seen);
   if (A.staged) {   // δ into shared memory, validated once
-    for (size_t i = tid; i < (size_t)k * n; i += bd) {
-      const uint32_t d = A.delta[i];
-      bad |= d >= n;
-      d16[i] = (uint16_t)(d < n ? d : 0u);
-    }
+    stage_delta(A.delta, (size_t)k * n, n, d16, &bad);
     if (bad) atomicOr(&s_flag, ERR_BAD_DELTA);
   }
-  const uint32_t any_acc = block_sum((seen & 1u) ? 1u : 0u, s_red) != 0u;
-  const uint32_t any_rej = block_sum((seen & 2u) ? 1u : 0u, s_red) != 0u;
+  const uint32_t classes = block_sum(((seen & 1u) ? 1u : 0u) | ((seen & 2u) ? 0x10000u : 0u), s_red);
+  const uint32_t any_acc = (classes & 0xFFFFu) != 0u, any_rej = (classes >> 16) != 0u;
   uint32_t B_prev = any_acc + any_rej, B_r = B_prev;
   uint32_t r = 0, changed = 0, cur = 0, maxed = 0, err = s_flag, w = 1;
+  uint32_t nt = 0;   // trace entries (thread 0)
+  if (tid == 0) trace_put(C, nt, t0, kTraceStart);
   // δ(q, a): the shared copy, or global memory (an invalid target reads as 0 and is reported)
   auto target = [&](uint32_t a, uint32_t q) -> uint32_t {
     if (A.staged) return d16[(size_t)a * n + q];
@@ -103,8 +98,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
     return d;
   };
   for (r = 1; !err; ++r) {
-    const uint16_t *src = lab[cur];
-    uint16_t *dst = lab[cur ^ 1u];
+    const uint16_t *src = cur ? lab1 : lab0;
+    uint16_t *dst = cur ? lab0 : lab1;
     const uint32_t K = (k + 1u) * w;
     const uint32_t mode = (K <= kSmallDirectBits && K <= A.log2T) ? 0u : K <= 31u ? 3u : (A.wide_table && K <= 63u) ? 1u : 2u;
     const uint32_t words = mode == 0u ? (1u << K) : (mode == 1u ? 2u * T : T);   // packed 32-bit keys (3): T words
@@ -193,6 +188,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
     }
     if (bad) atomicOr(&s_flag, ERR_BAD_DELTA);
     B_r = block_sum(created, s_red);   // includes the barriers that end the round
+    if (tid == 0) trace_put(C, nt, t0, kTraceRound | (mode << 4));
     cur ^= 1u;
     w = mode == 0u ? K : A.log2T;   // table rounds: labels are slots
     if (s_flag) {   // every thread reads it after the same barrier: a uniform decision
@@ -227,12 +223,12 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
   }
   // canonical numbering: blocks in order of their smallest state (every label
   // is below T: a slot, or a direct signature of at most log2 T bits)
-  const uint16_t *fin = lab[cur];
+  const uint16_t *fin = cur ? lab1 : lab0;
   uint32_t blocks = B_r;
   if (B_r == n) {
     for (uint32_t q = tid; q < n; q += bd) A.out[q] = q;
   } else {
-    uint16_t *rank = lab[cur ^ 1u];   // free now: rank of each block's smallest state
+    uint16_t *rank = cur ? lab0 : lab1;   // free now: rank of each block's smallest state
     for (uint32_t i = tid; i < T; i += bd) tbl[i] = 0xFFFFFFFFu;
     __syncthreads();
     for (uint32_t q = tid; q < n; q += bd) atomicMin(&tbl[fin[q]], q);
@@ -253,6 +249,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
     blocks = total;
   }
   if (tid == 0) {
+    trace_put(C, nt, t0, kTraceEnd);
     C->rounds_executed = r;
     C->rounds_changed = changed;
     C->num_blocks = blocks;
@@ -271,7 +268,7 @@ static SmallPlan small_plan(uint32_t n, uint32_t k) {
   SmallPlan p{};
   p.log2T = ceil_log2(n + n / 2 < 64 ? 64 : n + n / 2);
   const size_t T = (size_t)1 << p.log2T;
-  const size_t labels = 2 * (size_t)((n + 1u) & ~1u) * 2;
+  const size_t labels = 2 * (size_t)((n + 7u) & ~7u) * 2;
   p.wide = (uint64_t)(k + 1) * p.log2T <= 63 ? 1u : 0u;
   size_t table = T * (p.wide ? 8 : 4);   // also the direct rounds' flags (2^log2T words at most)
   if (table + labels > kSmallSmem && p.wide) {   // 64-bit slots do not fit: representatives
@@ -290,21 +287,25 @@ static SmallPlan small_plan(uint32_t n, uint32_t k) {
   return p;
 }
 
-// The single block is taken where it measured faster than the cooperative
-// kernel: when packed keys fit 64-bit slots, or up to 4,096 states whatever
-// the letters.  An explicit `schedule` (a width of the cooperative kernel),
-// the table-only and bucketed flags keep the cooperative kernel.
+// Up to kSmallMaxStates states the cluster kernel is taken where the device
+// can place its cluster; otherwise (or with DFA_FLAG_ONE_BLOCK) the single
+// block, where it measured faster than the cooperative kernel: when packed
+// keys fit 64-bit slots, or up to 4,096 states whatever the letters.  An
+// explicit `schedule` (a width of the cooperative kernel), the table-only and
+// bucketed flags keep the cooperative kernel.
 bool small_fits(uint32_t n, uint32_t k, const dfa_opts &o) {
   if (o.algo != DFA_ALGO_MOORE) return false;
   if (o.schedule >= 1) return false;
   if (o.flags & (DFA_FLAG_BUCKETED | DFA_FLAG_TABLE_ONLY)) return false;
   if (n < 1 || n > kSmallMaxStates) return false;
+  if (cluster_fits(n, k, o)) return true;
   const SmallPlan p = small_plan(n, k);
   return p.smem != 0 && (p.wide || n <= 4096);
 }
 
 int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
                   const dfa_opts &o, cudaStream_t st) {
+  if (cluster_fits(n, k, o)) return enqueue_cluster(delta, accept, n, k, out, ctrl, o, st);
   const SmallPlan p = small_plan(n, k);
   if (p.smem == 0) return fail(DFA_EINVAL, "the single-block kernel does not fit %u states", n);
   SmallArgs a{};

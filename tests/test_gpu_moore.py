@@ -56,31 +56,66 @@ def test_random_sizes_ragged(g, n, k):
     _assert_parity(g, A)
 
 
-@pytest.mark.parametrize("n", [1, 2, 7, 63, 65, 513, 4097, 10_000, 16_384])
-@pytest.mark.parametrize("k", [0, 2, 5])
-def test_small_sizes_both_kernels(g, n, k):
-    """Up to 16,384 states the default call runs the single-block kernel; an
-    explicit schedule (1) runs the cooperative kernel.  Both equal the oracle."""
+@pytest.mark.parametrize("n", [1, 2, 7, 8, 9, 63, 65, 127, 129, 513, 4097, 10_000, 16_383, 16_384])
+@pytest.mark.parametrize("k", [0, 1, 2, 5, 9])
+def test_small_sizes_all_kernels(g, n, k):
+    """Up to 16,384 states the default call runs the cluster kernel (where the
+    GPU places its cluster); DFA_FLAG_ONE_BLOCK runs the single-block kernel,
+    and an explicit schedule (1) the cooperative kernel.  All equal the oracle.
+    Sizes span slices that end inside a CTA, CTAs with no states, and
+    signatures wide enough for the representative comparison (k = 9)."""
     A = dfagen.random_dfa(n, k, 0.5, 5000 + n + k)
     ref = oracle.moore(A.delta, A.accept)
     _assert_parity(g, A, ref)
+    _assert_parity(g, A, ref, flags=g.DFA_FLAG_ONE_BLOCK)
     _assert_parity(g, A, ref, schedule=1)
 
 
-def test_small_kernel_deep_chain_and_limits(g):
-    """The single-block kernel on the 16,384-state chain: 16,383 rounds to the
-    fixpoint; a round limit and a time limit end it with their statuses."""
+@pytest.mark.parametrize("n,k,copies", [(2000, 2, 8), (500, 4, 30), (300, 12, 40), (3000, 3, 5)])
+def test_small_kernels_real_merges(g, n, k, copies):
+    """Planted redundancy (every block has several members) on the cluster and
+    single-block kernels, against the oracle and Hopcroft's partition."""
+    base = dfagen.random_dfa(n, k, 0.5, 70 + n)
+    A, _ = dfagen.planted_redundancy(base, copies, 71 + k)
+    if A.n > 16_384:
+        pytest.skip("beyond the small kernels")
+    ref = oracle.moore(A.delta, A.accept)
+    assert np.array_equal(ref.block, oracle.hopcroft(A.delta, A.accept))
+    stop = oracle.moore(A.delta, A.accept, stop_discrete=True)
+    for flags in (0, g.DFA_FLAG_ONE_BLOCK):
+        _assert_parity(g, A, ref, flags=flags)
+        _assert_parity(g, A, stop, flags=flags | g.DFA_FLAG_STOP_DISCRETE)
+
+
+@pytest.mark.parametrize("one_block", [False, True])
+def test_small_kernel_deep_chain_and_limits(g, one_block):
+    """The small kernels on the 16,384-state chain: 16,383 rounds to the
+    fixpoint; a round limit and a time limit end them with their statuses."""
+    flags = g.DFA_FLAG_ONE_BLOCK if one_block else 0
     C = dfagen.chain_dfa(16_384)
-    res = _assert_parity(g, C)
+    res = _assert_parity(g, C, flags=flags)
     assert res.rounds_changed == 16_382
     d, a = _dev(C)
-    block, res = g.minimise(d, a, max_rounds=7, check=False)
+    block, res = g.minimise(d, a, max_rounds=7, check=False, flags=flags)
     assert res.call_status == g.DFA_EMAXROUNDS and res.rounds_executed == 7
     ref = oracle.moore(C.delta, C.accept, max_rounds=7)
     assert np.array_equal(block.cpu().numpy().view(np.uint32), oracle.canonical(ref.block))
-    _, res = g.minimise(d, a, timeout_ns=200_000, check=False)    # 0.2 ms: far below the work needed
+    _, res = g.minimise(d, a, timeout_ns=200_000, check=False, flags=flags)   # 0.2 ms: far below the work
     assert res.call_status == g.DFA_ETIMEOUT
-    _assert_parity(g, dfagen.random_dfa(4096, 2, 0.5, 1))          # the context survives
+    _assert_parity(g, dfagen.random_dfa(4096, 2, 0.5, 1), flags=flags)     # the context survives
+
+
+def test_small_kernels_bad_target(g):
+    """An invalid transition target is reported by both small kernels (staged
+    δ and δ read from global memory), and the context survives."""
+    for n, k in ((1000, 2), (16_000, 12)):
+        A = dfagen.random_dfa(n, k, 0.5, 77)
+        A.delta[k - 1][n // 2] = n
+        d, a = _dev(A)
+        for flags in (0, g.DFA_FLAG_ONE_BLOCK):
+            _, res = g.minimise(d, a, check=False, flags=flags)
+            assert res.call_status == g.DFA_EINVAL
+    _assert_parity(g, dfagen.random_dfa(1000, 2, 0.5, 78))
 
 
 @pytest.mark.parametrize("schedule", [1, 2, 4])
