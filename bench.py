@@ -258,7 +258,7 @@ def extras(g):
     dev, one, coop = [], [], []
     for _ in range(20):
         dev.append(g.minimise(d, a)[1].device_ns)
-        one.append(g.minimise(d, a, flags=g.DFA_FLAG_ONE_BLOCK)[1].device_ns)
+        one.append(g.minimise(d, a, flags=g.DFA_FLAG_ONE_BLOCK)[1].device_ns)   # forced single block
         coop.append(g.minimise(d, a, schedule=1)[1].device_ns)
     cpu1 = _best_of(lambda: oracle.moore_c(A.delta, A.accept, threads=1), 5)
     cpuN = _best_of(lambda: oracle.moore_c(A.delta, A.accept, threads=0), 5)

@@ -111,9 +111,13 @@ typedef enum dfa_algo {
 #define DFA_FLAG_GATHER 0x10u    /* signature refinement: never use the bucketed gather, even with
                                       DFA_FLAG_BUCKETED set; same results */
 #define DFA_FLAG_ONE_BLOCK 0x20u /* signature refinement of a DFA of at most 16,384 states: run
-                                      it in one thread block instead of one thread-block cluster
-                                      (the default where the GPU can place the cluster); same
-                                      results.  Honoured by dfa_minimise and dfa_minimise_async. */
+                                      it in one thread block where it fits (else the cooperative
+                                      kernel); same results.  Honoured by dfa_minimise and
+                                      dfa_minimise_async. */
+#define DFA_FLAG_CLUSTER 0x40u   /* the same on one thread-block cluster where the GPU can place it
+                                      (else the cooperative kernel); without either flag the call
+                                      picks the cluster from 6,144 states on, or where one block
+                                      does not fit; same results. */
 
 typedef struct dfa_opts {
   int32_t algo;            /* dfa_algo */
@@ -151,12 +155,13 @@ size_t dfa_workspace_size(const dfa_t *dfa, const dfa_opts *opts);
  * Section 2 treats their removal as a separate pre-processing step).
  * block_out: n uint32 (device or host).  res: host struct.  opts may be NULL
  * (Moore, no round limit, default time limit).  Signature refinement of a DFA
- * of at most 16,384 states runs on one thread-block cluster (8 or 16 blocks;
- * labels replicated and the renumbering table distributed over the blocks'
- * shared memory) where the GPU can place it, else (and with
- * DFA_FLAG_ONE_BLOCK) in one thread block with its labels, table and (when
- * they fit) transitions in shared memory, when its packed signatures fit 63
- * bits or it has at most 4,096 states; larger DFAs, DFA_FLAG_TABLE_ONLY,
+ * of at most 16,384 states runs in one thread block with its labels, table
+ * and (when they fit) transitions in shared memory, when its packed
+ * signatures fit 63 bits or it has at most 4,096 states, up to 6,143 states;
+ * from 6,144 states on, or where one block does not fit, on one thread-block
+ * cluster (8 or 16 blocks; labels replicated and the renumbering table
+ * distributed over the blocks' shared memory) where the GPU can place it
+ * (DFA_FLAG_ONE_BLOCK and DFA_FLAG_CLUSTER force either); larger DFAs, DFA_FLAG_TABLE_ONLY,
  * DFA_FLAG_BUCKETED and an explicit schedule run the cooperative kernel over
  * the whole GPU.  The results are the same. */
 int dfa_minimise(const dfa_t *dfa, const dfa_opts *opts, uint32_t *block_out, dfa_result *res,

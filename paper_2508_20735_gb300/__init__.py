@@ -30,6 +30,7 @@ DFA_FLAG_STOP_DISCRETE = 0x4
 DFA_FLAG_BUCKETED = 0x8
 DFA_FLAG_GATHER = 0x10
 DFA_FLAG_ONE_BLOCK = 0x20
+DFA_FLAG_CLUSTER = 0x40
 DFA_REQ_MINIMISE, DFA_REQ_EQUIVALENT = 0, 1
 
 

@@ -59,8 +59,8 @@ bool small_fits(uint32_t n, uint32_t k, const dfa_opts &o);
 int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
                   const dfa_opts &o, cudaStream_t st);
 // The same on one thread-block cluster (cluster.cu), where the device can place
-// one and the DFA fits; enqueue_small takes it unless DFA_FLAG_ONE_BLOCK is set.
-bool cluster_fits(uint32_t n, uint32_t k, const dfa_opts &o);
+// one and the DFA fits; enqueue_small decides between the two.
+bool cluster_fits(uint32_t n, uint32_t k);
 int enqueue_cluster(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
                     const dfa_opts &o, cudaStream_t st);
 

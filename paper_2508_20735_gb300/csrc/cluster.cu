@@ -369,8 +369,7 @@ static uint32_t cluster_log2_size() {
   return best;
 }
 
-bool cluster_fits(uint32_t n, uint32_t k, const dfa_opts &o) {
-  if (o.flags & DFA_FLAG_ONE_BLOCK) return false;
+bool cluster_fits(uint32_t n, uint32_t k) {
   const uint32_t l2 = cluster_log2_size();
   ClusterPlan p;
   return l2 != 0 && cluster_plan(n, k, l2, &p);

@@ -287,25 +287,41 @@ static SmallPlan small_plan(uint32_t n, uint32_t k) {
   return p;
 }
 
-// Up to kSmallMaxStates states the cluster kernel is taken where the device
-// can place its cluster; otherwise (or with DFA_FLAG_ONE_BLOCK) the single
-// block, where it measured faster than the cooperative kernel: when packed
-// keys fit 64-bit slots, or up to 4,096 states whatever the letters.  An
-// explicit `schedule` (a width of the cooperative kernel), the table-only and
-// bucketed flags keep the cooperative kernel.
-bool small_fits(uint32_t n, uint32_t k, const dfa_opts &o) {
-  if (o.algo != DFA_ALGO_MOORE) return false;
-  if (o.schedule >= 1) return false;
-  if (o.flags & (DFA_FLAG_BUCKETED | DFA_FLAG_TABLE_ONLY)) return false;
-  if (n < 1 || n > kSmallMaxStates) return false;
-  if (cluster_fits(n, k, o)) return true;
+// Which small kernel refines a DFA, if any.  Up to kSmallMaxStates states: the
+// single block where it fits and measured faster than the cooperative kernel
+// (packed keys fit 64-bit slots, or at most 4,096 states whatever the
+// letters); the cluster kernel from kClusterMinStates states on, or where the
+// single block does not fit, when the device can place its cluster.  The
+// cluster's barrier and distributed-shared-memory traffic cost more than they
+// save below about 6,000 states (4,096 states, 2 letters: 21 against 20 us;
+// 10,000 states: 27 against 42 us).  DFA_FLAG_ONE_BLOCK and DFA_FLAG_CLUSTER
+// force one of the two where it fits.  An explicit `schedule` (a width of the
+// cooperative kernel), the table-only and bucketed flags keep the cooperative
+// kernel.
+enum SmallKernel { SK_NONE = 0, SK_ONE_BLOCK, SK_CLUSTER };
+static constexpr uint32_t kClusterMinStates = 6144;
+
+static SmallKernel pick_small(uint32_t n, uint32_t k, const dfa_opts &o) {
+  if (o.algo != DFA_ALGO_MOORE) return SK_NONE;
+  if (o.schedule >= 1) return SK_NONE;
+  if (o.flags & (DFA_FLAG_BUCKETED | DFA_FLAG_TABLE_ONLY)) return SK_NONE;
+  if (n < 1 || n > kSmallMaxStates) return SK_NONE;
   const SmallPlan p = small_plan(n, k);
-  return p.smem != 0 && (p.wide || n <= 4096);
+  const bool one = p.smem != 0 && (p.wide || n <= 4096);
+  if (o.flags & DFA_FLAG_ONE_BLOCK) return one ? SK_ONE_BLOCK : SK_NONE;
+  const bool cl = cluster_fits(n, k);
+  if (o.flags & DFA_FLAG_CLUSTER) return cl ? SK_CLUSTER : SK_NONE;
+  if (one && n < kClusterMinStates) return SK_ONE_BLOCK;
+  if (cl) return SK_CLUSTER;
+  return one ? SK_ONE_BLOCK : SK_NONE;
 }
+
+bool small_fits(uint32_t n, uint32_t k, const dfa_opts &o) { return pick_small(n, k, o) != SK_NONE; }
 
 int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
                   const dfa_opts &o, cudaStream_t st) {
-  if (cluster_fits(n, k, o)) return enqueue_cluster(delta, accept, n, k, out, ctrl, o, st);
+  const SmallKernel which = pick_small(n, k, o);
+  if (which == SK_CLUSTER) return enqueue_cluster(delta, accept, n, k, out, ctrl, o, st);
   const SmallPlan p = small_plan(n, k);
   if (p.smem == 0) return fail(DFA_EINVAL, "the single-block kernel does not fit %u states", n);
   SmallArgs a{};

@@ -59,15 +59,17 @@ def test_random_sizes_ragged(g, n, k):
 @pytest.mark.parametrize("n", [1, 2, 7, 8, 9, 63, 65, 127, 129, 513, 4097, 10_000, 16_383, 16_384])
 @pytest.mark.parametrize("k", [0, 1, 2, 5, 9])
 def test_small_sizes_all_kernels(g, n, k):
-    """Up to 16,384 states the default call runs the cluster kernel (where the
-    GPU places its cluster); DFA_FLAG_ONE_BLOCK runs the single-block kernel,
-    and an explicit schedule (1) the cooperative kernel.  All equal the oracle.
-    Sizes span slices that end inside a CTA, CTAs with no states, and
-    signatures wide enough for the representative comparison (k = 9)."""
+    """Up to 16,384 states the default call picks the single-block or the
+    cluster kernel; DFA_FLAG_ONE_BLOCK and DFA_FLAG_CLUSTER force either (the
+    cooperative kernel where it does not fit), and an explicit schedule (1)
+    runs the cooperative kernel.  All equal the oracle.  Sizes span slices
+    that end inside a CTA, CTAs with no states, and signatures wide enough for
+    the representative comparison (k = 9)."""
     A = dfagen.random_dfa(n, k, 0.5, 5000 + n + k)
     ref = oracle.moore(A.delta, A.accept)
     _assert_parity(g, A, ref)
     _assert_parity(g, A, ref, flags=g.DFA_FLAG_ONE_BLOCK)
+    _assert_parity(g, A, ref, flags=g.DFA_FLAG_CLUSTER)
     _assert_parity(g, A, ref, schedule=1)
 
 
@@ -82,7 +84,7 @@ def test_small_kernels_real_merges(g, n, k, copies):
     ref = oracle.moore(A.delta, A.accept)
     assert np.array_equal(ref.block, oracle.hopcroft(A.delta, A.accept))
     stop = oracle.moore(A.delta, A.accept, stop_discrete=True)
-    for flags in (0, g.DFA_FLAG_ONE_BLOCK):
+    for flags in (g.DFA_FLAG_CLUSTER, g.DFA_FLAG_ONE_BLOCK):
         _assert_parity(g, A, ref, flags=flags)
         _assert_parity(g, A, stop, flags=flags | g.DFA_FLAG_STOP_DISCRETE)
 
@@ -91,7 +93,7 @@ def test_small_kernels_real_merges(g, n, k, copies):
 def test_small_kernel_deep_chain_and_limits(g, one_block):
     """The small kernels on the 16,384-state chain: 16,383 rounds to the
     fixpoint; a round limit and a time limit end them with their statuses."""
-    flags = g.DFA_FLAG_ONE_BLOCK if one_block else 0
+    flags = g.DFA_FLAG_ONE_BLOCK if one_block else g.DFA_FLAG_CLUSTER
     C = dfagen.chain_dfa(16_384)
     res = _assert_parity(g, C, flags=flags)
     assert res.rounds_changed == 16_382
@@ -112,7 +114,7 @@ def test_small_kernels_bad_target(g):
         A = dfagen.random_dfa(n, k, 0.5, 77)
         A.delta[k - 1][n // 2] = n
         d, a = _dev(A)
-        for flags in (0, g.DFA_FLAG_ONE_BLOCK):
+        for flags in (0, g.DFA_FLAG_ONE_BLOCK, g.DFA_FLAG_CLUSTER):
             _, res = g.minimise(d, a, check=False, flags=flags)
             assert res.call_status == g.DFA_EINVAL
     _assert_parity(g, dfagen.random_dfa(1000, 2, 0.5, 78))
