@@ -124,9 +124,11 @@ typedef struct dfa_opts {
   uint32_t max_rounds;     /* 0 = no limit; otherwise DFA_EMAXROUNDS after this many rounds */
   uint64_t timeout_ns;     /* 0 = library default (600 s); limit on the whole call's device work */
   int32_t schedule;        /* -1 = autotune / default; >= 0 selects a kernel schedule.  Batch
-                              calls: 0..5, 1 + (s & 1) states per lane and 256 >> (s >> 1)
-                              states per tile (DFA_EINVAL beyond 5; -1 lets the autotuner time
-                              all six once per batch shape, see dfa_minimise_batch).
+                              calls: 0..11, 1 + (s & 1) states per lane, 256 >> ((s >> 1) % 3)
+                              states per tile, and from 6 on every DFA that fits one thread
+                              block refined alone by one block (DFA_EINVAL beyond 11; -1 lets
+                              the autotuner time all twelve once per batch shape, see
+                              dfa_minimise_batch).
                               dfa_minimise: 1, 2 or 4 forces the cooperative kernel with that
                               many states per thread (the default runs DFAs of at most 16,384
                               states in one thread block when they fit, see dfa_minimise) */
@@ -179,13 +181,14 @@ size_t dfa_batch_workspace_size(const dfa_t *dfas, uint32_t count, const dfa_opt
  * The DFAs' arrays may live anywhere (host or device), independently.
  * Schedules (dfa_opts.schedule): with -1 the first call for a batch shape (GPU,
  * total states and batch size rounded up to powers of two, largest k) runs the
- * batch under all six schedules and keeps the fastest by device time; the
+ * batch under all twelve schedules and keeps the fastest by device time; the
  * choice and every schedule's time are kept in memory and in the JSON file
  * $DFA_AUTOTUNE_CACHE (default ~/.cache/dfa_gb300_autotune.json), one line per
- * shape: "batch|<GPU>|states2^a|dfas2^b|kmaxc": [choice, ns_0, ..., ns_5].
- * The launch is a CUDA graph (control-block reset + the cooperative kernel),
- * instantiated once per host thread and schedule's lane width and updated in
- * place by later calls (dfa_batch_graph_stats counts both). */
+ * shape: "batch|<GPU>|states2^a|dfas2^b|kmaxc": [choice, ns_0, ..., ns_11].
+ * The launch is a CUDA graph (control-block reset + the cooperative kernel,
+ * then for schedules 6..11 the kernel that refines the DFAs fitting one block
+ * one per block), instantiated once per host thread and graph shape and
+ * updated in place by later calls (dfa_batch_graph_stats counts both). */
 int dfa_minimise_batch(const dfa_t *dfas, uint32_t count, const dfa_opts *opts, uint32_t *block_out,
                        dfa_result *res, void *workspace, size_t ws_bytes, void *stream);
 

@@ -58,6 +58,28 @@ static constexpr uint32_t kSmallMaxStates = 16384;
 bool small_fits(uint32_t n, uint32_t k, const dfa_opts &o);
 int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
                   const dfa_opts &o, cudaStream_t st);
+// Batches (batch.cu): a DFA refined alone by one thread block of small.cu's
+// kernel; plan = log2 T | wide table << 8 | staged δ << 9 (small_block_plan).
+struct BatchSmallItem {
+  const uint32_t *delta;   // device, k x n letter-major
+  const uint8_t *accept;   // device, n
+  uint32_t n, k;
+  uint32_t *out;           // device, n canonical block numbers
+  uint32_t *ss;            // device, the DFA's bookkeeping row
+  uint32_t plan, pad_;
+};
+// Indices, in a bookkeeping row, of the words the block writes.
+struct BatchSmallWords {
+  uint32_t b, changed, executed, maxed;
+};
+// Whether one block holds the DFA (shared memory), its plan and shared memory.
+bool small_block_plan(uint32_t n, uint32_t k, uint32_t *plan, size_t *smem);
+// One block per SM at most (grid), each refining the next item from *next (zeroed);
+// batch_small_setup (outside any stream capture) allows the kernel its shared memory.
+cudaError_t batch_small_setup();
+cudaError_t enqueue_batch_small(const BatchSmallItem *items, uint32_t count, uint32_t *next, Ctrl *ctrl, size_t smem,
+                                BatchSmallWords words, const dfa_opts &o, uint32_t grid, cudaStream_t st);
+
 // The same on one thread-block cluster (cluster.cu), where the device can place
 // one and the DFA fits; enqueue_small decides between the two.
 bool cluster_fits(uint32_t n, uint32_t k);

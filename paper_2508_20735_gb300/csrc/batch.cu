@@ -40,15 +40,22 @@ static constexpr size_t kMaxGridB = 8192;
 
 // Schedules of the batch kernel, chosen per call (opts.schedule) or by the
 // autotuner: states per lane within a tile pass (1, two blocks of 512 threads
-// per SM; or 2, one block per SM with room for twice the keys) and states per
+// per SM; or 2, one block per SM with room for twice the keys), states per
 // tile (256, 128 or 64: smaller tiles balance the passes between grid barriers
-// better and cost more per-tile bookkeeping).  Schedule s takes 1 + (s & 1)
-// states per lane and 256 >> (s >> 1) states per tile.
-static constexpr int kBatchSchedules = 6;
+// better and cost more per-tile bookkeeping), and whether every DFA that fits
+// one thread block's shared memory is refined alone by one block instead
+// (after the cooperative launch, which then refines only the others; a block
+// per DFA needs no grid barrier at all).  Schedule s (0..11) takes
+// 1 + (s & 1) states per lane, 256 >> ((s >> 1) % 3) states per tile, and
+// blocks per DFA from s = 6 on.
+static constexpr int kBatchSchedules = 12;
 struct BatchSchedule {
   uint32_t vec, tile;
+  bool blocks;
 };
-static inline BatchSchedule batch_schedule(int s) { return BatchSchedule{1u + (uint32_t)(s & 1), 256u >> (s >> 1)}; }
+static inline BatchSchedule batch_schedule(int s) {
+  return BatchSchedule{1u + (uint32_t)(s & 1), 256u >> ((s >> 1) % 3), s >= 6};
+}
 
 struct SegInfo {
   const uint32_t *delta;   // device
@@ -58,6 +65,8 @@ struct SegInfo {
   uint32_t log2S;          // table region of 2^log2S slots
   uint32_t wid;            // bits of a local state number (labels of filter rounds)
   uint64_t table_off;      // first slot of the region
+  uint32_t small;          // 1: refined alone by one thread block after this kernel (skipped here)
+  uint32_t pad_;
 };
 
 struct Tile {
@@ -541,7 +550,7 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
   for (uint64_t i = tid; i < A.total_slots; i += stride) reinterpret_cast<uint4 *>(A.table)[i] = make_uint4(0, 0, 0, 0);
   for (uint64_t i = tid; i < bm_words; i += stride) A.bm[1][i] = 0u;
   for (uint32_t i = tid; i < A.nsegs; i += stride) {
-    A.ss[i * SS_WORDS + SS_ACTIVE] = 1u;
+    A.ss[i * SS_WORDS + SS_ACTIVE] = A.segs[i].small ? 0u : 1u;
     A.ss[i * SS_WORDS + SS_FINAL] = 1u;
     A.ss[i * SS_WORDS + SS_W] = 1u;
     A.ss[i * SS_WORDS + SS_FOK] = 1u;
@@ -707,7 +716,7 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
     for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
-      if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
+      if (S.small || A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
       const uint64_t region = 1ull << S.log2S;
       const uint32_t nt = A.tile_off[T.seg + 1] - A.tile_off[T.seg], j = t - A.tile_off[T.seg];
       const uint64_t per = (region + nt - 1) / nt, lo = (uint64_t)j * per;
@@ -721,7 +730,7 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
     for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
-      if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
+      if (S.small || A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
       const uint32_t *fl = A.lab[A.ss[T.seg * SS_WORDS + SS_FINAL]] + S.state_off;
       for (uint32_t base = 0; base < T.len; base += 32) {
         const bool valid = base + lane < T.len;
@@ -739,8 +748,8 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
     for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
-      uint32_t c = T.len;
-      if (A.ss[T.seg * SS_WORDS + SS_B] != S.n) {
+      uint32_t c = S.small ? 0u : T.len;
+      if (!S.small && A.ss[T.seg * SS_WORDS + SS_B] != S.n) {
         const uint32_t *fl = A.lab[A.ss[T.seg * SS_WORDS + SS_FINAL]] + S.state_off;
         c = 0;
         for (uint32_t base = 0; base < T.len; base += 32) {
@@ -761,6 +770,7 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
       uint32_t *o = A.out + S.state_off;
+      if (S.small) continue;
       if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) {
         for (uint32_t i = lane; i < T.len; i += 32) o[T.start + i] = T.start + i;
         continue;
@@ -786,7 +796,7 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
     for (uint32_t t = next_tile(A, &s_next); t < A.ntiles; t = next_tile(A, &s_next)) {
       const Tile T = A.tiles[t];
       const SegInfo &S = A.segs[T.seg];
-      if (A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
+      if (S.small || A.ss[T.seg * SS_WORDS + SS_B] == S.n) continue;
       const uint32_t *fl = A.lab[A.ss[T.seg * SS_WORDS + SS_FINAL]] + S.state_off;
       for (uint32_t i = lane; i < T.len; i += 32) {
         const uint32_t q = T.start + i;
@@ -804,7 +814,7 @@ __global__ void __launch_bounds__(kBatchThreads, VEC == 1 ? 2 : 1) batch_kernel(
 
 struct BatchLayout {
   size_t ctrl, segs, tile_off, tiles, lab0, lab1, tmp, tmp2, seen1, seen2, seen3, seen4, rep, dups, dups2, dups3, table,
-      bm0, bm1, minrep, tile_cnt, tile_pre, partials, out, cnt, ss, stage, total;
+      bm0, bm1, minrep, tile_cnt, tile_pre, partials, out, cnt, ss, items, small_next, stage, total;
   size_t list_entries;
   uint32_t mbits;
   uint64_t total_states, total_slots;
@@ -937,6 +947,8 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchIn
   L.out = take(st * 4);
   L.cnt = take((size_t)count * 3 * 4);
   L.ss = take((size_t)count * SS_WORDS * 4);
+  L.items = take((size_t)count * sizeof(BatchSmallItem));
+  L.small_next = take(4);
   L.stage_bytes = stage_bytes;
   L.stage = take(stage_bytes);
   L.total = off;
@@ -966,18 +978,19 @@ static size_t batch_max_warps() {
   return best;
 }
 
-// Launches the batch kernel as a CUDA graph: the control-block reset and the
-// cooperative launch are captured on a library-owned stream (capture is not
-// allowed on the legacy default stream) and the graph runs on `st`.  The
-// instantiated graph is kept per host thread and per kernel variant: a later
-// call captures its own two nodes (new pointers, new grid) and moves them into
-// the kept executable with cudaGraphExecUpdate, which costs a fraction of a new
-// instantiation; only when the update is refused is the graph instantiated
-// again.  An update affects later launches only, and launches of one
-// executable run in order, so a call never changes a launch still in flight.
+// The DFAs of a batch refined one per block after the cooperative launch.
+struct SmallLaunch {
+  const BatchSmallItem *items;   // device
+  uint32_t count;
+  uint32_t *next;                // device word, zeroed in the graph
+  size_t smem;
+  uint32_t grid;
+  const dfa_opts *o;
+};
+
 struct GraphCache {
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};   // by states per lane - 1
+  cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};   // by lane width and block-per-DFA part
   ~GraphCache() {   // at thread exit; errors are ignored (the runtime may be gone at process exit)
     for (cudaGraphExec_t &x : exec)
       if (x) cudaGraphExecDestroy(x);
@@ -987,7 +1000,17 @@ struct GraphCache {
 static thread_local GraphCache g_graphs;
 static std::atomic<uint64_t> g_graph_instantiations{0}, g_graph_updates{0};
 
-static cudaError_t launch_batch_graph(const BatchArgs &a, int grid, cudaStream_t st) {
+// Launches the batch kernel as a CUDA graph: the control-block reset and the
+// cooperative launch (then, with `sl`, the reset of the DFA counter and the
+// block-per-DFA kernel) are captured on a library-owned stream (capture is not
+// allowed on the legacy default stream) and the graph runs on `st`.  The
+// instantiated graph is kept per host thread and per kernel variant: a later
+// call captures its own nodes (new pointers, new grid) and moves them into the
+// kept executable with cudaGraphExecUpdate, which costs a fraction of a new
+// instantiation; only when the update is refused is the graph instantiated
+// again.  An update affects later launches only, and launches of one
+// executable run in order, so a call never changes a launch still in flight.
+static cudaError_t launch_batch_graph(const BatchArgs &a, int grid, const SmallLaunch *sl, cudaStream_t st) {
   GraphCache &G = g_graphs;
   cudaError_t e;
   if (!G.cap && (e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
@@ -999,13 +1022,19 @@ static cudaError_t launch_batch_graph(const BatchArgs &a, int grid, cudaStream_t
   cudaError_t le = cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), G.cap);
   if (le == cudaSuccess)
     le = cudaLaunchCooperativeKernel(batch_kernel_for(a.vec), dim3(grid), dim3(kBatchThreads), params, 0, G.cap);
+  if (le == cudaSuccess && sl) {
+    le = cudaMemsetAsync(sl->next, 0, 4, G.cap);
+    const BatchSmallWords words{SS_B, SS_CHANGED, SS_EXECUTED, SS_MAXED};
+    if (le == cudaSuccess)
+      le = enqueue_batch_small(sl->items, sl->count, sl->next, a.ctrl, sl->smem, words, *sl->o, sl->grid, G.cap);
+  }
   e = cudaStreamEndCapture(G.cap, &graph);
   if (le != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     return le;
   }
   if (e != cudaSuccess) return e;
-  cudaGraphExec_t &exec = G.exec[a.vec == 2 ? 1 : 0];
+  cudaGraphExec_t &exec = G.exec[(a.vec == 2 ? 1 : 0) + (sl ? 2 : 0)];
   bool updated = false;
   if (exec) {
     cudaGraphExecUpdateResultInfo info{};
@@ -1037,7 +1066,7 @@ static cudaError_t launch_batch_graph(const BatchArgs &a, int grid, cudaStream_t
 // keeps the fastest by device time, and remembers the choice together with
 // every schedule's time, in memory and in a JSON file ($DFA_AUTOTUNE_CACHE,
 // default ~/.cache/dfa_gb300_autotune.json), one entry per line:
-//   "batch|<GPU>|states2^a|dfas2^b|kmaxc": [choice, ns_0, ns_1, ..., ns_5]
+//   "batch|<GPU>|states2^a|dfas2^b|kmaxc": [choice, ns_0, ns_1, ..., ns_11]
 // Later calls with the same key run the remembered schedule directly.
 struct TuneEntry {
   int choice = -1;
@@ -1146,8 +1175,8 @@ static size_t batch_workspace_impl(const dfa_t *dfas, uint32_t count, const Batc
   uint32_t kmax;
   if (check_batch(dfas, count, &total, &kmax) != DFA_OK) return 0;
   size_t most = 0;
-  for (int sc = 0; sc < kBatchSchedules; ++sc) {   // the workspace serves every schedule
-    const BatchLayout L = batch_layout(dfas, count, in, batch_schedule(sc).tile, nullptr, nullptr, nullptr);
+  for (uint32_t tile : {256u, 128u, 64u}) {   // the workspace serves every schedule (they differ by tile)
+    const BatchLayout L = batch_layout(dfas, count, in, tile, nullptr, nullptr, nullptr);
     if (L.total_slots > 0xFFFFFFFFull) return 0;
     most = std::max(most, L.total);
   }
@@ -1207,6 +1236,31 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
       segs[i].accept = reinterpret_cast<const uint8_t *>(p);
     }
   }
+  const bool ho = !is_device_ptr(block_out);
+  uint32_t *out_dev = ho ? reinterpret_cast<uint32_t *>(ws + L.out) : block_out;
+  // block per DFA: every DFA whose refinement fits one block's shared memory,
+  // largest first
+  std::vector<BatchSmallItem> items;
+  size_t small_smem = 0;
+  if (batch_schedule(schedule).blocks) {
+    for (uint32_t i = 0; i < count; ++i) {
+      uint32_t plan;
+      size_t sm;
+      if (!small_block_plan(segs[i].n, segs[i].k, &plan, &sm)) continue;
+      segs[i].small = 1u;
+      small_smem = std::max(small_smem, sm);
+      items.push_back(BatchSmallItem{segs[i].delta, segs[i].accept, segs[i].n, segs[i].k,
+                                     out_dev + segs[i].state_off,
+                                     reinterpret_cast<uint32_t *>(ws + L.ss) + (size_t)i * SS_WORDS, plan, 0u});
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const BatchSmallItem &x, const BatchSmallItem &y) { return x.n > y.n; });
+    if (!items.empty()) {
+      e = cudaMemcpyAsync(ws + L.items, items.data(), sizeof(BatchSmallItem) * items.size(), cudaMemcpyHostToDevice,
+                          st);
+      if (e != cudaSuccess) return cuda_fail(e, "copy block-per-DFA items");
+    }
+  }
   e = cudaMemcpyAsync(ws + L.segs, segs.data(), sizeof(SegInfo) * count, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "copy segment table");
   e = cudaMemcpyAsync(ws + L.tile_off, tile_off.data(), tile_off.size() * 4, cudaMemcpyHostToDevice, st);
@@ -1214,7 +1268,6 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
   e = cudaMemsetAsync(ws + L.cnt, 0, (size_t)count * 3 * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.ss, 0, (size_t)count * SS_WORDS * 4, st);
   if (e != cudaSuccess) return cuda_fail(e, "clear batch bookkeeping");
-  const bool ho = !is_device_ptr(block_out);
   BatchArgs a{};
   a.segs = reinterpret_cast<const SegInfo *>(ws + L.segs);
   a.nsegs = count;
@@ -1243,7 +1296,7 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
   a.tile_cnt = reinterpret_cast<uint32_t *>(ws + L.tile_cnt);
   a.tile_pre = reinterpret_cast<uint32_t *>(ws + L.tile_pre);
   a.partials = reinterpret_cast<uint32_t *>(ws + L.partials);
-  a.out = ho ? reinterpret_cast<uint32_t *>(ws + L.out) : block_out;
+  a.out = out_dev;
   a.cnt = reinterpret_cast<uint32_t *>(ws + L.cnt);
   a.ss = reinterpret_cast<uint32_t *>(ws + L.ss);
   a.ctrl = reinterpret_cast<Ctrl *>(ws + L.ctrl);
@@ -1268,7 +1321,17 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
   if ((size_t)grid * (kBatchThreads / 32) > batch_max_warps())
     return fail(DFA_ECUDA, "grid larger than the workspace was sized for");
   a.dup_cap = (uint32_t)(((size_t)L.ntiles + grid - 1) / grid * tile);
-  e = launch_batch_graph(a, grid, st);
+  SmallLaunch sl{};
+  if (!items.empty()) {
+    if ((e = batch_small_setup()) != cudaSuccess) return cuda_fail(e, "shared memory of the block-per-DFA kernel");
+    sl.items = reinterpret_cast<const BatchSmallItem *>(ws + L.items);
+    sl.count = (uint32_t)items.size();
+    sl.next = reinterpret_cast<uint32_t *>(ws + L.small_next);
+    sl.smem = small_smem;
+    sl.grid = (uint32_t)std::min<size_t>((size_t)sms, items.size());
+    sl.o = &o;
+  }
+  e = launch_batch_graph(a, grid, items.empty() ? nullptr : &sl, st);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch of the batch kernel");
   Ctrl c{};
   std::vector<uint32_t> ss((size_t)count * SS_WORDS);

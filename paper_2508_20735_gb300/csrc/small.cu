@@ -51,8 +51,16 @@ __device__ __forceinline__ uint32_t small_mix(uint32_t h, uint32_t v) {
   return h * 0x85EBCA6Bu;
 }
 
-__global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __grid_constant__ SmallArgs A) {
-  extern __shared__ __align__(16) uint32_t sm[];
+// What one refinement in a block produced.
+struct SmallOut {
+  uint32_t err, rounds_executed, rounds_changed, num_blocks, maxed;
+};
+
+// The refinement of one DFA by the calling block (every thread takes part),
+// with the canonical numbering written to A.out.  sm: the block's dynamic
+// shared memory; C: control block for the trace (thread 0), or null; t0: the
+// start time the call's time limit counts from.
+__device__ __forceinline__ SmallOut small_refine(const SmallArgs &A, uint32_t *sm, Ctrl *C, unsigned long long t0) {
   __shared__ uint32_t s_red[32];
   __shared__ uint32_t s_flag;   // ERR_BAD_DELTA seen by any thread (read after the round's last barrier)
   __shared__ uint32_t s_stop;   // the call's time limit ran out (thread 0 decides between rounds)
@@ -65,12 +73,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
   uint16_t *const lab0 = reinterpret_cast<uint16_t *>(sm + twords), *const lab1 = lab0 + ((n + 7u) & ~7u);
   uint16_t *d16 = lab1 + ((n + 7u) & ~7u);                      // k n halfwords when staged
   volatile uint32_t *vtbl = tbl;
-  Ctrl *C = A.ctrl;
-  const unsigned long long t0 = gtimer();
-  if (tid == 0) {
-    C->t_start = t0;
-    s_flag = 0u;
-  }
+  if (tid == 0) s_flag = 0u;
   __syncthreads();   // s_flag is clear before any thread reports into it
   // the initial partition {F, Q \ F}: labels 0/1, B_0 = the classes present
   // (16-byte loads where the arrays allow, several in flight per thread: the
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
   uint32_t B_prev = any_acc + any_rej, B_r = B_prev;
   uint32_t r = 0, changed = 0, cur = 0, maxed = 0, err = s_flag, w = 1;
   uint32_t nt = 0;   // trace entries (thread 0)
-  if (tid == 0) trace_put(C, nt, t0, kTraceStart);
+  if (tid == 0 && C) trace_put(C, nt, t0, kTraceStart);
   // δ(q, a): the shared copy, or global memory (an invalid target reads as 0 and is reported)
   auto target = [&](uint32_t a, uint32_t q) -> uint32_t {
     if (A.staged) return d16[(size_t)a * n + q];
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
     }
     if (bad) atomicOr(&s_flag, ERR_BAD_DELTA);
     B_r = block_sum(created, s_red);   // includes the barriers that end the round
-    if (tid == 0) trace_put(C, nt, t0, kTraceRound | (mode << 4));
+    if (tid == 0 && C) trace_put(C, nt, t0, kTraceRound | (mode << 4));
     cur ^= 1u;
     w = mode == 0u ? K : A.log2T;   // table rounds: labels are slots
     if (s_flag) {   // every thread reads it after the same barrier: a uniform decision
@@ -214,13 +217,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
     }
     B_prev = B_r;
   }
-  if (err) {
-    if (tid == 0) {
-      C->err = err;
-      C->t_end = gtimer();
-    }
-    return;
-  }
+  if (err) return SmallOut{err, r, changed, 0u, maxed};
   // canonical numbering: blocks in order of their smallest state (every label
   // is below T: a slot, or a direct signature of at most log2 T bits)
   const uint16_t *fin = cur ? lab1 : lab0;
@@ -248,14 +245,77 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
     for (uint32_t q = tid; q < n; q += bd) A.out[q] = tbl[fin[q]] & 0x7FFFFFFFu;
     blocks = total;
   }
-  if (tid == 0) {
-    trace_put(C, nt, t0, kTraceEnd);
-    C->rounds_executed = r;
-    C->rounds_changed = changed;
-    C->num_blocks = blocks;
-    C->maxed = maxed;
+  if (tid == 0 && C) trace_put(C, nt, t0, kTraceEnd);
+  return SmallOut{0u, r, changed, blocks, maxed};
+}
+
+__global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __grid_constant__ SmallArgs A) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  Ctrl *C = A.ctrl;
+  const unsigned long long t0 = gtimer();
+  if (threadIdx.x == 0) C->t_start = t0;
+  const SmallOut o = small_refine(A, sm, C, t0);
+  if (threadIdx.x == 0) {
+    if (o.err) {
+      C->err = o.err;
+    } else {
+      C->rounds_executed = o.rounds_executed;
+      C->rounds_changed = o.rounds_changed;
+      C->num_blocks = o.num_blocks;
+      C->maxed = o.maxed;
+    }
     C->t_end = gtimer();
   }
+}
+
+// Batches: the DFAs of items[0, count) refined one per block, each block
+// taking the next DFA from *next (items sorted by decreasing size, so that the
+// largest start first); each block writes its DFA's partition and round counts
+// and adds its errors and its end time to the batch's control block.
+struct BatchSmallArgs {
+  const BatchSmallItem *items;
+  uint32_t count;
+  uint32_t *next;            // zeroed before the launch
+  Ctrl *ctrl;
+  BatchSmallWords words;     // where the results go in a DFA's bookkeeping row
+  uint32_t max_rounds, stop_discrete;
+  unsigned long long timeout_ns;
+};
+
+__global__ void __launch_bounds__(kSmallThreads, 1) batch_small_kernel(const __grid_constant__ BatchSmallArgs B) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ uint32_t s_i;
+  for (;;) {
+    if (threadIdx.x == 0) s_i = atomicAdd(B.next, 1u);
+    __syncthreads();
+    const uint32_t i = s_i;
+    __syncthreads();   // every thread has read s_i before the next DFA's refinement reuses the block
+    if (i >= B.count) break;
+    const BatchSmallItem &it = B.items[i];
+    SmallArgs a{};
+    a.delta = it.delta;
+    a.accept = it.accept;
+    a.n = it.n;
+    a.k = it.k;
+    a.out = it.out;
+    a.ctrl = nullptr;
+    a.log2T = it.plan & 0xFFu;
+    a.wide_table = (it.plan >> 8) & 1u;
+    a.staged = (it.plan >> 9) & 1u;
+    a.max_rounds = B.max_rounds;
+    a.stop_discrete = B.stop_discrete;
+    a.timeout_ns = B.timeout_ns;
+    const SmallOut o = small_refine(a, sm, nullptr, gtimer());
+    if (threadIdx.x == 0) {
+      if (o.err) atomicOr(&B.ctrl->err, o.err);
+      it.ss[B.words.b] = o.num_blocks;
+      it.ss[B.words.changed] = o.rounds_changed;
+      it.ss[B.words.executed] = o.rounds_executed;
+      it.ss[B.words.maxed] = o.maxed;
+    }
+    __syncthreads();   // the refinement's last reads of shared memory are done
+  }
+  if (threadIdx.x == 0) atomicMax(&B.ctrl->t_end, gtimer());
 }
 
 // Shared memory of the kernel for n states and k letters (smem 0: no fit).
@@ -345,6 +405,34 @@ int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "launch of the single-block kernel");
   return DFA_OK;
+}
+
+bool small_block_plan(uint32_t n, uint32_t k, uint32_t *plan, size_t *smem) {
+  if (n < 1 || n > kSmallMaxStates) return false;
+  const SmallPlan p = small_plan(n, k);
+  if (p.smem == 0) return false;
+  *plan = p.log2T | (p.wide << 8) | (p.staged << 9);
+  *smem = p.smem;
+  return true;
+}
+
+cudaError_t enqueue_batch_small(const BatchSmallItem *items, uint32_t count, uint32_t *next, Ctrl *ctrl, size_t smem,
+                                BatchSmallWords words, const dfa_opts &o, uint32_t grid, cudaStream_t st) {
+  BatchSmallArgs b{};
+  b.items = items;
+  b.count = count;
+  b.next = next;
+  b.ctrl = ctrl;
+  b.words = words;
+  b.max_rounds = o.max_rounds;
+  b.stop_discrete = (o.flags & DFA_FLAG_STOP_DISCRETE) ? 1u : 0u;
+  b.timeout_ns = o.timeout_ns;
+  batch_small_kernel<<<grid, kSmallThreads, smem, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_small_setup() {
+  return cudaFuncSetAttribute(batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmem);
 }
 
 }  // namespace dfa

@@ -51,7 +51,7 @@ def _mixed():
     return dfas
 
 
-@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4, 5, -1])
+@pytest.mark.parametrize("schedule", list(range(12)) + [-1])
 def test_mixed_batch_against_oracle(g, schedule):
     dfas = _mixed()
     blocks, res = _batch(g, dfas, schedule=schedule)
@@ -62,7 +62,7 @@ def test_mixed_batch_against_oracle(g, schedule):
             (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
 
 
-@pytest.mark.parametrize("schedule", [0, 5, -1])
+@pytest.mark.parametrize("schedule", [0, 5, 6, 11, -1])
 def test_mixed_batch_stop_discrete(g, schedule):
     dfas = _mixed()
     blocks, res = _batch(g, dfas, schedule=schedule, flags=g.DFA_FLAG_STOP_DISCRETE)
@@ -74,7 +74,7 @@ def test_mixed_batch_stop_discrete(g, schedule):
 
 
 def test_autotuner_records_every_schedule(g):
-    """The autotuner times all six schedules once per batch shape, keeps the
+    """The autotuner times all twelve schedules once per batch shape, keeps the
     fastest, and writes the choice and every time to its cache file."""
     import json
     dfas = [dfagen.random_dfa(n, k, 0.3, 950 + i) for i, (n, k) in enumerate(
@@ -88,13 +88,13 @@ def test_autotuner_records_every_schedule(g):
     assert kmax, cache
     entry = cache[kmax[0]]
     choice, times = entry[0], entry[1:]
-    assert len(times) == 6 and all(t > 0 for t in times)
-    assert 0 <= choice < 6 and times[choice] == min(times)
+    assert len(times) == 12 and all(t > 0 for t in times)
+    assert 0 <= choice < 12 and times[choice] == min(times)
 
 
 def test_batch_schedule_out_of_range(g):
     with pytest.raises(g.DfaError) as e:
-        _batch(g, [dfagen.random_dfa(100, 2, 0.5, 3)], schedule=6)
+        _batch(g, [dfagen.random_dfa(100, 2, 0.5, 3)], schedule=12)
     assert e.value.status == g.DFA_EINVAL
 
 
@@ -147,6 +147,37 @@ def test_batch_4096_full_size(g):
         d, a = _dev(A)
         alone, ra = g.minimise(d, a)
         assert np.array_equal(b, alone.cpu().numpy().view(np.uint32)), i
+
+
+@pytest.mark.parametrize("schedule", [0, 6])
+def test_batch_recipe_both_paths(g, schedule):
+    """512 DFAs of the batch recipe, sizes from 64 to 65,536 states: with
+    schedule 6 the DFAs that fit one block are refined one per block and the
+    rest by the cooperative kernel, in the same call; every partition and
+    round count equals the oracle's."""
+    dfas = dfagen.batch_dfas(512, 64, 65_536, 2, 8, 0.3, 41)
+    assert any(A.n > 16_384 for A in dfas) and any(A.n <= 16_384 for A in dfas)
+    blocks, res = _batch(g, dfas, schedule=schedule)
+    for i, (A, b, r) in enumerate(zip(dfas, blocks, res)):
+        ref = oracle.moore(A.delta, A.accept)
+        assert np.array_equal(b, ref.block), i
+        assert (r.num_blocks, r.rounds_changed, r.rounds_executed) == \
+            (ref.num_blocks, ref.rounds_changed, ref.rounds_executed), i
+
+
+def test_batch_block_per_dfa_limits(g):
+    """Round limit and an invalid target on the block-per-DFA path."""
+    dfas = [dfagen.chain_dfa(50), dfagen.random_dfa(100, 2, 0.5, 3), dfagen.random_dfa(30_000, 3, 0.5, 4)]
+    blocks, res = _batch(g, dfas, schedule=6, max_rounds=3, check=False)
+    for A, b, r in zip(dfas, blocks, res):
+        ref = oracle.moore(A.delta, A.accept, max_rounds=3)
+        assert np.array_equal(b, oracle.canonical(ref.block))
+        assert r.rounds_executed == ref.rounds_executed
+    assert res[0].status == g.DFA_EMAXROUNDS
+    B = dfagen.random_dfa(50, 2, 0.5, 4)
+    B.delta[1][7] = 50
+    with pytest.raises(g.DfaError):
+        _batch(g, [dfagen.random_dfa(100, 2, 0.5, 3), B], schedule=6)
 
 
 def test_batch_max_rounds(g):
