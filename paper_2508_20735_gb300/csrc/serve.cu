@@ -646,6 +646,7 @@ struct dfa_server {
   std::string worker_error;
   // counters (under mu): steps run, requests and states advanced by one round, host time in steps
   uint64_t steps = 0, request_rounds = 0, state_rounds = 0;
+  bool front_blocked = false;   // a request held on the host waits for arena space (under mu)
   uint64_t mode_state_rounds[3] = {0, 0, 0};   // by round mode: direct, filter, table
   double step_us = 0.0;
 };
@@ -734,23 +735,34 @@ static void worker_main(dfa_server *s) {
       if (s->active.empty())
         s->cv_work.wait_for(lock, std::chrono::milliseconds(50), [&] { return s->stop || !s->queue.empty(); });
       if (s->stop) break;
-      // admission in arrival order while a slot and arena space are free
+      // admission in arrival order while a slot and arena space are free.  A
+      // request held on the host that finds no arena space blocks the requests
+      // held on the host behind it, but not those already placed in the arena
+      // at submit (they need no space; were they to wait, the space they hold
+      // could never come back and the front could wait forever); while the
+      // front is blocked, submissions stop taking arena space early.
       size_t tiles_now = 0;
       for (auto &r : s->active) tiles_now += r->ntiles;
-      while (!s->queue.empty() && s->active.size() < s->max_slots) {
-        auto r = s->queue.front();
+      bool blocked = false;
+      for (auto it = s->queue.begin(); it != s->queue.end() && s->active.size() < s->max_slots;) {
+        auto r = *it;
         const size_t want_tiles = (r->n + kServeTile - 1) / kServeTile;
         if (tiles_now + want_tiles > max_tiles) break;
         if (!r->early) {
           size_t off;
-          if (!s->arena->alloc(r->bytes, &off)) break;
+          if (blocked || !s->arena->alloc(r->bytes, &off)) {
+            blocked = true;
+            ++it;
+            continue;
+          }
           r->off = off;
         }
-        s->queue.pop_front();
+        it = s->queue.erase(it);
         s->active.push_back(r);
         admitted.push_back(r);
         tiles_now += want_tiles;
       }
+      s->front_blocked = blocked;
     }
     for (auto &r : admitted) {
       const cudaError_t e = place_req(s, *r);
@@ -1084,7 +1096,7 @@ int dfa_serve_submit(dfa_server *s, int kind, const dfa_t *a, const dfa_t *b, co
     {
       std::lock_guard<std::mutex> lock(s->mu);
       size_t off;
-      if (s->arena->alloc(r->bytes, &off)) {
+      if (!s->front_blocked && s->arena->alloc(r->bytes, &off)) {   // the blocked front goes first
         r->off = off;
         r->early = true;
       }

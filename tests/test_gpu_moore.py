@@ -424,3 +424,24 @@ def test_many_letters_large_against_oracle(g):
     A = dfagen.random_dfa((1 << 20) + 3, 8, 0.5, 21)
     _assert_parity(g, A, ref=oracle.moore(A.delta, A.accept))
 
+
+
+@pytest.mark.parametrize("n,k", [(1000, 2), (10_000, 3), (333, 5)])
+def test_small_kernels_unaligned_inputs(g, n, k):
+    """δ and the acceptance bytes at addresses that are not 16-byte aligned
+    (4 bytes and 1 byte past an aligned start): the small kernels stage them
+    with plain loads instead of 16-byte ones, and the cooperative kernel picks
+    its narrow width; the results equal the oracle's."""
+    import torch
+    A = dfagen.random_dfa(n, k, 0.5, 600 + n + k)
+    ref = oracle.moore(A.delta, A.accept)
+    dbuf = torch.zeros(k * n + 1, dtype=torch.int32, device="cuda")
+    dbuf[1:] = torch.from_numpy(np.ascontiguousarray(A.delta).view(np.int32).ravel()).cuda()
+    abuf = torch.zeros(n + 3, dtype=torch.uint8, device="cuda")
+    abuf[3:] = torch.from_numpy(np.ascontiguousarray(A.accept)).cuda()
+    d, a = dbuf[1:], abuf[3:]
+    assert d.data_ptr() % 16 != 0 and a.data_ptr() % 16 != 0
+    for kw in ({"flags": g.DFA_FLAG_ONE_BLOCK}, {"flags": g.DFA_FLAG_CLUSTER}, {}, {"schedule": 1}):
+        block, res = g.minimise(d.view(k, n), a, **kw)
+        assert np.array_equal(block.cpu().numpy().view(np.uint32), ref.block)
+        assert (res.rounds_changed, res.rounds_executed) == (ref.rounds_changed, ref.rounds_executed)

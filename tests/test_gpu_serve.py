@@ -199,3 +199,48 @@ def test_served_equivalence_recipe_full_sizes(g):
             ref = alone[i % 32]
             assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
                 (ref.num_blocks, ref.rounds_changed, ref.rounds_executed)
+
+
+def test_small_and_large_requests_with_limits(g):
+    """A mix of small and large requests (unions from a few hundred to over
+    100,000 states; minimisation, equivalence with and without early exit,
+    round limits on a small and a large chain) gives every request the
+    stand-alone call's result and the oracle's partition."""
+    reqs = []
+    for i in range(10):
+        A, B, eq = dfagen.equivalence_pair(100 + i, 9, n_lo=300, n_hi=60_000)
+        reqs.append(("eq", (A, B, eq), i % 2 == 0))
+    for i, n in enumerate((700, 9000, 16_384, 16_385, 50_000)):
+        reqs.append(("min", dfagen.random_dfa(n, 2 + i % 3, 0.5, 800 + i), 0))
+    chain = dfagen.chain_dfa(3000)
+    reqs.append(("min", chain, 5))            # small path, stopped by the round limit
+    reqs.append(("min", dfagen.chain_dfa(20_000), 7))   # step path, stopped by the round limit
+    assert any(kind == "eq" and x[0].n + x[1].n <= 16_384 for kind, x, _ in reqs)
+    assert any(kind == "eq" and x[0].n + x[1].n > 16_384 for kind, x, _ in reqs)
+    with g.Server(4 << 30, max_slots=16) as srv:
+        tickets = []
+        for kind, item, opt in reqs:
+            if kind == "min":
+                tickets.append(srv.submit_minimise(item.delta, item.accept, max_rounds=opt))
+            else:
+                A, B, _ = item
+                tickets.append(srv.submit_equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start),
+                                                     early_exit=opt))
+        for (kind, item, opt), t in zip(reqs, tickets):
+            if kind == "min":
+                st, res, _, blocks = srv.wait(t, n=item.n)
+                ref = oracle.moore(item.delta, item.accept, max_rounds=opt or None)
+                # the limit ends the call only while every round still splits a block
+                assert st == (g.DFA_EMAXROUNDS if opt and ref.rounds_changed == opt else g.DFA_OK)
+                assert np.array_equal(blocks, oracle.canonical(ref.block))
+                assert (res.rounds_changed, res.rounds_executed) == (ref.rounds_changed, ref.rounds_executed)
+            else:
+                A, B, expect = item
+                st, res, eq, _ = srv.wait(t)
+                assert st == g.DFA_OK and eq == int(expect)
+                alone_eq, alone = g.equivalent((A.delta, A.accept, A.start), (B.delta, B.accept, B.start),
+                                               early_exit=opt)
+                assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
+                    (alone.num_blocks, alone.rounds_changed, alone.rounds_executed)
+        c = srv.counters()
+        assert c["state_rounds"] == c["state_rounds_direct"] + c["state_rounds_filter"] + c["state_rounds_table"]
