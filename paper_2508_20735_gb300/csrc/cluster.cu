@@ -5,7 +5,9 @@
 // cluster, else 8) instead of the one SM that the single-block kernel
 // (small.cu) issues from.  Per CTA, in shared memory:
 //  * both label arrays of all n states (16-bit; every CTA holds a full copy);
-//  * when they fit, all k n transitions as 16-bit targets;
+//  * the transitions as 16-bit targets: only the rows of the CTA's own slice
+//    when no round can compare representatives (packed keys of at most 63
+//    bits), else all k n of them when they fit;
 //  * its share of the renumbering table: the table has T = 2^log2T > n slots
 //    of 64 bits, and CTA c owns slots [c T/C, (c+1) T/C).  Two tables alternate
 //    by round parity, so that a CTA clears the one of the next round while the
@@ -57,7 +59,9 @@ struct ClusterArgs {
   uint32_t log2T;          // table slots (all CTAs) 2^log2T > n; labels stay below 2^log2T
   uint32_t log2C;          // CTAs in the cluster: 2^log2C
   uint32_t per;            // states per CTA slice (a multiple of 8)
-  uint32_t staged;         // 1: every CTA copies δ into shared memory as 16-bit targets
+  uint32_t staged;         // 16-bit targets in shared memory: 0 none (global reads), 1 all of δ in every
+                           // CTA, 2 the rows of the CTA's own slice only (k x per; possible whenever
+                           // no round compares representatives, which need any state's successors)
   uint32_t max_rounds;     // 0 = none
   uint32_t stop_discrete;  // 1: stop after a round that leaves n blocks
   unsigned long long timeout_ns;
@@ -71,9 +75,9 @@ __host__ __device__ inline size_t cluster_label_bytes(uint32_t per, uint32_t log
   return (size_t)per << log2C << 2;   // two arrays of C*per halfwords
 }
 __host__ __device__ inline size_t cluster_region_bytes(uint32_t n, uint32_t k, uint32_t log2T, uint32_t log2C,
-                                                       uint32_t staged) {
+                                                       uint32_t staged, uint32_t per) {
   const size_t shares = 2 * (((size_t)1 << log2T) >> log2C) * 8;
-  const size_t rounds = shares + (staged ? (size_t)k * n * 2 : 0);
+  const size_t rounds = shares + (staged == 1 ? (size_t)k * n * 2 : staged == 2 ? (size_t)k * per * 2 : 0);
   const size_t numbering = ((size_t)1 << log2T) * 4;
   return rounds > numbering ? rounds : numbering;
 }
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) moore_cluster_kernel(const
   const uint32_t np = A.per << A.log2C;                                           // label array length
   uint16_t *const lab0 = csm, *const lab1 = csm + np;
   unsigned long long *const share0 = reinterpret_cast<unsigned long long *>(csm + 2 * np), *const share1 = share0 + S;
-  uint16_t *d16 = reinterpret_cast<uint16_t *>(share1 + S);   // k n halfwords when staged
+  uint16_t *d16 = reinterpret_cast<uint16_t *>(share1 + S);   // k n (staged 1) or k per (staged 2) halfwords
   uint32_t *numtab = reinterpret_cast<uint32_t *>(csm + 2 * np);  // numbering: over the shares and δ
   Ctrl *Cc = A.ctrl;
   const unsigned long long t0 = gtimer();
@@ -114,14 +118,36 @@ __global__ void __launch_bounds__(kClusterThreads, 1) moore_cluster_kernel(const
   // staging is latency-bound otherwise)
   uint32_t seen = 0, bad = 0;
   stage_accept(A.accept, n, lab0, &seen);
-  if (A.staged) stage_delta(A.delta, (size_t)k * n, n, d16, &bad);
+  const uint32_t q0 = me * A.per, q1 = q0 + A.per < n ? q0 + A.per : n;   // this CTA's slice
+  if (A.staged == 1) {
+    stage_delta(A.delta, (size_t)k * n, n, d16, &bad);
+  } else if (A.staged == 2 && q0 < q1) {   // k rows of the slice, one batch of loads for all of them
+    const uint32_t len = q1 - q0, tot = k * A.per;
+    for (uint32_t base = 0; base < tot; base += 4u * bd) {
+      uint32_t v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t i = base + j * bd + tid, a = i / A.per, x = i - a * A.per;
+        v[j] = i < tot && x < len ? A.delta[(size_t)a * n + q0 + x] : 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t i = base + j * bd + tid;
+        if (i < tot) {
+          bad |= v[j] >= n;
+          d16[i] = (uint16_t)(v[j] < n ? v[j] : 0u);
+        }
+      }
+    }
+  }
   for (uint32_t i = tid; i < 2u * S; i += bd) share0[i] = 0ull;   // share1 follows share0
   if (bad) atomicOr(&s_bad, ERR_BAD_DELTA);
   const uint32_t classes = block_sum(((seen & 1u) ? 1u : 0u) | ((seen & 2u) ? 0x10000u : 0u), s_red);
   const uint32_t any_acc = (classes & 0xFFFFu) != 0u, any_rej = (classes >> 16) != 0u;
   __syncthreads();
-  // every CTA staged all of δ, so s_bad is the same everywhere
-  uint32_t err = s_bad;
+  // with all of δ staged every CTA saw every target, so s_bad is the same
+  // everywhere; otherwise it joins the first round's words (read alike by all)
+  uint32_t err = A.staged == 1 ? s_bad : 0u;
   cl.sync();   // table shares clear before any remote insert
   uint32_t nt = 0;   // trace entries (CTA 0, thread 0)
   if (me == 0 && tid == 0) trace_put(Cc, nt, t0, kTraceStart);
@@ -129,7 +155,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) moore_cluster_kernel(const
   uint32_t r = 0, changed = 0, cur = 0, maxed = 0, w = 1;
   // δ(q, a): the shared copy, or global memory (an invalid target reads as 0 and is reported)
   auto target = [&](uint32_t a, uint32_t q) -> uint32_t {
-    if (A.staged) return d16[(size_t)a * n + q];
+    if (A.staged == 1) return d16[(size_t)a * n + q];
+    if (A.staged == 2) return d16[(size_t)a * A.per + (q - q0)];   // q in this CTA's slice
     uint32_t d = A.delta[(size_t)a * n + q];
     if (d >= n) {
       bad = 1u;
@@ -141,7 +168,6 @@ __global__ void __launch_bounds__(kClusterThreads, 1) moore_cluster_kernel(const
   auto slot_ptr = [&](unsigned long long *tab, uint32_t g) -> unsigned long long * {
     return cl.map_shared_rank(tab, g >> log2S) + (g & (S - 1u));
   };
-  const uint32_t q0 = me * A.per, q1 = q0 + A.per < n ? q0 + A.per : n;
   for (r = 1; !err; ++r) {
     const uint16_t *src = cur ? lab1 : lab0;
     uint16_t *dst = cur ? lab0 : lab1;
@@ -319,9 +345,12 @@ static bool cluster_plan(uint32_t n, uint32_t k, uint32_t log2C, ClusterPlan *p)
   const uint32_t C = 1u << log2C;
   p->per = ((n + C - 1) / C + 7) / 8 * 8;
   const size_t labels = cluster_label_bytes(p->per, log2C);
-  for (uint32_t staged : {1u, 0u}) {
+  // a round compares representatives when its packed keys exceed 63 bits:
+  // then any state's successors are needed, else only the slice's own
+  const bool compare = (uint64_t)(k + 1) * p->log2T > 63;
+  for (uint32_t staged : {compare ? 1u : 2u, 0u}) {
     p->staged = staged;
-    p->smem = labels + cluster_region_bytes(n, k, p->log2T, log2C, staged);
+    p->smem = labels + cluster_region_bytes(n, k, p->log2T, log2C, staged, p->per);
     if (p->smem <= kClusterSmem) return true;
   }
   return false;
