@@ -59,15 +59,23 @@ bool small_fits(uint32_t n, uint32_t k, const dfa_opts &o);
 int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
                   const dfa_opts &o, cudaStream_t st);
 // Batches (batch.cu): a DFA refined alone by one thread block of small.cu's
-// kernel; plan = log2 T | wide table << 8 | staged δ << 9 (small_block_plan).
+// kernel; plan = log2 T | wide table << 8 | staged δ << 9 (small_block_plan:
+// everything in shared memory), or log2 T | 1 << 10 (medium_block_plan: up to
+// 65,536 states, labels in shared memory, the table at `table` in global
+// memory, two n-word scratch arrays).
 struct BatchSmallItem {
   const uint32_t *delta;   // device, k x n letter-major
   const uint8_t *accept;   // device, n
   uint32_t n, k;
   uint32_t *out;           // device, n canonical block numbers
   uint32_t *ss;            // device, the DFA's bookkeeping row
+  uint32_t *table;         // medium plan: 2^log2T words of global memory
+  uint32_t *scratch0, *scratch1;   // medium plan: n words each
   uint32_t plan, pad_;
 };
+// The medium plan of a DFA of n states whose table region has 2^log2S
+// 16-byte slots (false beyond 65,536 states).
+bool medium_block_plan(uint32_t n, uint32_t log2S, uint32_t *plan, size_t *smem);
 // Indices, in a bookkeeping row, of the words the block writes.
 struct BatchSmallWords {
   uint32_t b, changed, executed, maxed;

@@ -990,7 +990,7 @@ struct SmallLaunch {
 
 struct GraphCache {
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};   // by lane width and block-per-DFA part
+  cudaGraphExec_t exec[6] = {};   // by graph shape: cooperative launch (lane width) or none, block kernel or none
   ~GraphCache() {   // at thread exit; errors are ignored (the runtime may be gone at process exit)
     for (cudaGraphExec_t &x : exec)
       if (x) cudaGraphExecDestroy(x);
@@ -1001,8 +1001,9 @@ static thread_local GraphCache g_graphs;
 static std::atomic<uint64_t> g_graph_instantiations{0}, g_graph_updates{0};
 
 // Launches the batch kernel as a CUDA graph: the control-block reset and the
-// cooperative launch (then, with `sl`, the reset of the DFA counter and the
-// block-per-DFA kernel) are captured on a library-owned stream (capture is not
+// cooperative launch (left out when every DFA has a block of its own; then,
+// with `sl`, the reset of the DFA counter and the block-per-DFA kernel) are
+// captured on a library-owned stream (capture is not
 // allowed on the legacy default stream) and the graph runs on `st`.  The
 // instantiated graph is kept per host thread and per kernel variant: a later
 // call captures its own nodes (new pointers, new grid) and moves them into the
@@ -1010,7 +1011,8 @@ static std::atomic<uint64_t> g_graph_instantiations{0}, g_graph_updates{0};
 // instantiation; only when the update is refused is the graph instantiated
 // again.  An update affects later launches only, and launches of one
 // executable run in order, so a call never changes a launch still in flight.
-static cudaError_t launch_batch_graph(const BatchArgs &a, int grid, const SmallLaunch *sl, cudaStream_t st) {
+static cudaError_t launch_batch_graph(const BatchArgs &a, int grid, bool coop, const SmallLaunch *sl,
+                                      cudaStream_t st) {
   GraphCache &G = g_graphs;
   cudaError_t e;
   if (!G.cap && (e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
@@ -1020,7 +1022,7 @@ static cudaError_t launch_batch_graph(const BatchArgs &a, int grid, const SmallL
   BatchArgs copy = a;
   void *params[] = {&copy};
   cudaError_t le = cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), G.cap);
-  if (le == cudaSuccess)
+  if (le == cudaSuccess && coop)
     le = cudaLaunchCooperativeKernel(batch_kernel_for(a.vec), dim3(grid), dim3(kBatchThreads), params, 0, G.cap);
   if (le == cudaSuccess && sl) {
     le = cudaMemsetAsync(sl->next, 0, 4, G.cap);
@@ -1034,7 +1036,7 @@ static cudaError_t launch_batch_graph(const BatchArgs &a, int grid, const SmallL
     return le;
   }
   if (e != cudaSuccess) return e;
-  cudaGraphExec_t &exec = G.exec[(a.vec == 2 ? 1 : 0) + (sl ? 2 : 0)];
+  cudaGraphExec_t &exec = G.exec[(coop ? (a.vec == 2 ? 1 : 0) : 2) + (sl ? 3 : 0)];
   bool updated = false;
   if (exec) {
     cudaGraphExecUpdateResultInfo info{};
@@ -1238,20 +1240,36 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
   }
   const bool ho = !is_device_ptr(block_out);
   uint32_t *out_dev = ho ? reinterpret_cast<uint32_t *>(ws + L.out) : block_out;
-  // block per DFA: every DFA whose refinement fits one block's shared memory,
-  // largest first
+  // block per DFA: every DFA whose refinement one block can hold (all in
+  // shared memory, or up to 65,536 states with the labels in shared memory and
+  // the table in the DFA's own table region), largest first
   std::vector<BatchSmallItem> items;
   size_t small_smem = 0;
+  uint32_t coop_dfas = count;
   if (batch_schedule(schedule).blocks) {
     for (uint32_t i = 0; i < count; ++i) {
       uint32_t plan;
       size_t sm;
-      if (!small_block_plan(segs[i].n, segs[i].k, &plan, &sm)) continue;
+      BatchSmallItem it{};
+      if (small_block_plan(segs[i].n, segs[i].k, &plan, &sm)) {
+      } else if (medium_block_plan(segs[i].n, segs[i].log2S, &plan, &sm)) {
+        it.table = reinterpret_cast<uint32_t *>(ws + L.table) + segs[i].table_off * 4;   // 4 words a slot
+        it.scratch0 = reinterpret_cast<uint32_t *>(ws + L.lab0) + segs[i].state_off;
+        it.scratch1 = reinterpret_cast<uint32_t *>(ws + L.lab1) + segs[i].state_off;
+      } else {
+        continue;
+      }
       segs[i].small = 1u;
+      --coop_dfas;
       small_smem = std::max(small_smem, sm);
-      items.push_back(BatchSmallItem{segs[i].delta, segs[i].accept, segs[i].n, segs[i].k,
-                                     out_dev + segs[i].state_off,
-                                     reinterpret_cast<uint32_t *>(ws + L.ss) + (size_t)i * SS_WORDS, plan, 0u});
+      it.delta = segs[i].delta;
+      it.accept = segs[i].accept;
+      it.n = segs[i].n;
+      it.k = segs[i].k;
+      it.out = out_dev + segs[i].state_off;
+      it.ss = reinterpret_cast<uint32_t *>(ws + L.ss) + (size_t)i * SS_WORDS;
+      it.plan = plan;
+      items.push_back(it);
     }
     std::stable_sort(items.begin(), items.end(),
                      [](const BatchSmallItem &x, const BatchSmallItem &y) { return x.n > y.n; });
@@ -1331,7 +1349,7 @@ static int run_batch(const dfa_t *dfas, uint32_t count, const BatchInputs &in, c
     sl.grid = (uint32_t)std::min<size_t>((size_t)sms, items.size());
     sl.o = &o;
   }
-  e = launch_batch_graph(a, grid, items.empty() ? nullptr : &sl, st);
+  e = launch_batch_graph(a, grid, coop_dfas > 0, items.empty() ? nullptr : &sl, st);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch of the batch kernel");
   Ctrl c{};
   std::vector<uint32_t> ss((size_t)count * SS_WORDS);

@@ -249,6 +249,157 @@ __device__ __forceinline__ SmallOut small_refine(const SmallArgs &A, uint32_t *s
   return SmallOut{0u, r, changed, blocks, maxed};
 }
 
+// A DFA of at most 65,536 states refined by one block with its labels in
+// shared memory and its renumbering table in global memory (the batch's
+// block-per-DFA schedules, for DFAs the fully shared-memory refinement above
+// cannot hold).  A label is the state number of its block's representative
+// (so it fits 16 bits), one array of them in shared memory; a round writes the
+// new labels to global memory (`newlab`) and copies them back after a block
+// barrier.  Every round renumbers by representative comparison: a state hashes
+// its signature, and a slot holds the representative that first claimed it; a
+// state joins a slot's block only if its own label and every successor's label
+// equal the representative's (so a hash collision costs a probe, never a
+// merge).  Slots carry the round in their top 12 bits, so a slot of an earlier
+// round reads as free and the table is cleared only once per 4,095 rounds.
+struct MediumArgs {
+  const uint32_t *delta;   // k*n, letter-major (global)
+  const uint8_t *accept;   // n
+  uint32_t n, k;
+  uint32_t *out;           // n: canonical block numbers
+  uint32_t *table;         // 2^log2T slots (global): round << 20 | (representative + 1)
+  uint32_t log2T;
+  uint32_t *newlab;        // n words of global scratch: a round's new labels, then the ranks
+  uint32_t *minrep;        // n words of global scratch: each block's smallest state
+  uint32_t max_rounds, stop_discrete;
+  unsigned long long timeout_ns;
+};
+static constexpr uint32_t kMediumTagShift = 20;
+static constexpr uint32_t kMediumTagMax = (1u << (32 - kMediumTagShift)) - 1u;   // 4,095
+
+__device__ __forceinline__ SmallOut medium_refine(const MediumArgs &A, uint16_t *L, unsigned long long t0) {
+  __shared__ uint32_t s_red[32];
+  __shared__ uint32_t s_flag;
+  __shared__ uint32_t s_stop;
+  const uint32_t n = A.n, k = A.k, tid = threadIdx.x, bd = blockDim.x;
+  const uint32_t T = 1u << A.log2T, mask = T - 1u;
+  volatile uint32_t *vt = A.table;
+  if (tid == 0) s_flag = 0u;
+  for (uint32_t i = tid; i < T; i += bd) A.table[i] = 0u;   // no earlier round's slots
+  // the initial partition {F, Q \ F}: labels 0/1
+  uint32_t seen = 0, bad = 0;
+  stage_accept(A.accept, n, L, &seen);
+  const uint32_t classes = block_sum(((seen & 1u) ? 1u : 0u) | ((seen & 2u) ? 0x10000u : 0u), s_red);
+  uint32_t B_prev = ((classes & 0xFFFFu) != 0u) + ((classes >> 16) != 0u), B_r = B_prev;
+  uint32_t r = 0, changed = 0, maxed = 0, err = 0, tag = 0;
+  auto target = [&](uint32_t a, uint32_t q) -> uint32_t {
+    uint32_t d = A.delta[(size_t)a * n + q];
+    if (d >= n) {
+      bad |= 1u;
+      d = 0u;
+    }
+    return d;
+  };
+  for (r = 1;; ++r) {
+    if (++tag > kMediumTagMax) {   // the tags wrap: every slot is cleared
+      tag = 1;
+      for (uint32_t i = tid; i < T; i += bd) A.table[i] = 0u;
+    }
+    __syncthreads();   // the table (and last round's labels) ready
+    uint32_t created = 0;
+    bad = 0;
+    for (uint32_t q = tid; q < n; q += bd) {
+      const uint32_t lq = L[q];
+      unsigned long long h = (0x243F6A8885A308D3ull ^ lq) * 0x9E3779B97F4A7C15ull;
+      for (uint32_t a = 0; a < k; ++a) {
+        h ^= L[target(a, q)];
+        h *= 0x9E3779B97F4A7C15ull;
+        h ^= h >> 29;
+      }
+      uint32_t slot = (uint32_t)(h >> (64u - A.log2T)), label = q;
+      const uint32_t mine = (tag << kMediumTagShift) | (q + 1u);
+      // at most T slots, each looked at at most twice (a failed claim re-reads it)
+      bool placed = false;
+      for (uint32_t step = 0; step < 2u * T && !placed; ++step) {
+        uint32_t v = vt[slot];
+        if ((v >> kMediumTagShift) != tag) {   // free in this round: claim it
+          const uint32_t old = atomicCAS(&A.table[slot], v, mine);
+          if (old == v) {   // q represents a new block
+            ++created;
+            placed = true;
+            continue;
+          }
+          v = old;   // taken meanwhile (only by this round's claims): look at what took it
+          if ((v >> kMediumTagShift) != tag) continue;
+        }
+        const uint32_t p = (v & ((1u << kMediumTagShift) - 1u)) - 1u;
+        bool same = lq == L[p];
+        for (uint32_t a = 0; same && a < k; ++a) same = L[target(a, q)] == L[target(a, p)];
+        if (same) {   // q joins p's block
+          label = p;
+          placed = true;
+          continue;
+        }
+        slot = (slot + 1u) & mask;
+      }
+      if (!placed) bad |= 2u;   // no slot (cannot happen at a load of at most 1/4)
+      A.newlab[q] = label;
+    }
+    if (bad & 1u) atomicOr(&s_flag, ERR_BAD_DELTA);
+    if (bad & 2u) atomicOr(&s_flag, ERR_TABLE_FULL);
+    B_r = block_sum(created, s_red);   // its barriers also complete the round's new labels
+    for (uint32_t q = tid; q < n; q += bd) L[q] = (uint16_t)A.newlab[q];
+    if (s_flag) {   // read after the same barrier by every thread
+      err = s_flag;
+      break;
+    }
+    const bool grew = B_r != B_prev;
+    if (grew) ++changed;
+    if (!grew) break;   // Algorithm 4's until-test
+    if (A.stop_discrete && B_r == n) break;
+    if (A.max_rounds != 0u && r >= A.max_rounds) {
+      maxed = 1u;
+      break;
+    }
+    if ((r & 15u) == 0u) {
+      if (tid == 0) s_stop = gtimer() - t0 > A.timeout_ns ? 1u : 0u;
+      __syncthreads();
+      if (s_stop) {
+        err = ERR_TIMEOUT;
+        break;
+      }
+    }
+    B_prev = B_r;
+  }
+  if (err) return SmallOut{err, r, changed, 0u, maxed};
+  __syncthreads();   // the last labels are in shared memory
+  // canonical numbering: blocks in order of their smallest state (labels are
+  // representatives, so below n)
+  uint32_t blocks = B_r;
+  if (B_r == n) {
+    for (uint32_t q = tid; q < n; q += bd) A.out[q] = q;
+  } else {
+    for (uint32_t q = tid; q < n; q += bd) A.minrep[q] = 0xFFFFFFFFu;
+    __syncthreads();
+    for (uint32_t q = tid; q < n; q += bd) atomicMin(&A.minrep[L[q]], q);
+    __syncthreads();
+    const uint32_t per = (n + bd - 1) / bd;
+    const uint32_t q0 = tid * per < n ? tid * per : n, q1 = q0 + per < n ? q0 + per : n;
+    uint32_t c = 0;
+    for (uint32_t q = q0; q < q1; ++q) c += A.minrep[L[q]] == q;
+    uint32_t total;
+    uint32_t base = block_excl_scan(c, s_red, &total);
+    for (uint32_t q = q0; q < q1; ++q)
+      if (A.minrep[L[q]] == q) A.newlab[q] = base++;
+    __syncthreads();
+    for (uint32_t q = tid; q < n; q += bd)
+      if (A.minrep[L[q]] == q) A.minrep[L[q]] = 0x80000000u | A.newlab[q];
+    __syncthreads();
+    for (uint32_t q = tid; q < n; q += bd) A.out[q] = A.minrep[L[q]] & 0x7FFFFFFFu;
+    blocks = total;
+  }
+  return SmallOut{0u, r, changed, blocks, maxed};
+}
+
 __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __grid_constant__ SmallArgs A) {
   extern __shared__ __align__(16) uint32_t sm[];
   Ctrl *C = A.ctrl;
@@ -285,6 +436,7 @@ struct BatchSmallArgs {
 __global__ void __launch_bounds__(kSmallThreads, 1) batch_small_kernel(const __grid_constant__ BatchSmallArgs B) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ uint32_t s_i;
+  if (threadIdx.x == 0) atomicCAS(&B.ctrl->t_start, 0ull, gtimer());   // when no cooperative launch set it
   for (;;) {
     if (threadIdx.x == 0) s_i = atomicAdd(B.next, 1u);
     __syncthreads();
@@ -292,20 +444,38 @@ __global__ void __launch_bounds__(kSmallThreads, 1) batch_small_kernel(const __g
     __syncthreads();   // every thread has read s_i before the next DFA's refinement reuses the block
     if (i >= B.count) break;
     const BatchSmallItem &it = B.items[i];
-    SmallArgs a{};
-    a.delta = it.delta;
-    a.accept = it.accept;
-    a.n = it.n;
-    a.k = it.k;
-    a.out = it.out;
-    a.ctrl = nullptr;
-    a.log2T = it.plan & 0xFFu;
-    a.wide_table = (it.plan >> 8) & 1u;
-    a.staged = (it.plan >> 9) & 1u;
-    a.max_rounds = B.max_rounds;
-    a.stop_discrete = B.stop_discrete;
-    a.timeout_ns = B.timeout_ns;
-    const SmallOut o = small_refine(a, sm, nullptr, gtimer());
+    SmallOut o;
+    if ((it.plan >> 10) & 1u) {   // labels in shared memory, table in global memory
+      MediumArgs m{};
+      m.delta = it.delta;
+      m.accept = it.accept;
+      m.n = it.n;
+      m.k = it.k;
+      m.out = it.out;
+      m.table = it.table;
+      m.log2T = it.plan & 0xFFu;
+      m.newlab = it.scratch0;
+      m.minrep = it.scratch1;
+      m.max_rounds = B.max_rounds;
+      m.stop_discrete = B.stop_discrete;
+      m.timeout_ns = B.timeout_ns;
+      o = medium_refine(m, reinterpret_cast<uint16_t *>(sm), gtimer());
+    } else {                      // everything in shared memory
+      SmallArgs a{};
+      a.delta = it.delta;
+      a.accept = it.accept;
+      a.n = it.n;
+      a.k = it.k;
+      a.out = it.out;
+      a.ctrl = nullptr;
+      a.log2T = it.plan & 0xFFu;
+      a.wide_table = (it.plan >> 8) & 1u;
+      a.staged = (it.plan >> 9) & 1u;
+      a.max_rounds = B.max_rounds;
+      a.stop_discrete = B.stop_discrete;
+      a.timeout_ns = B.timeout_ns;
+      o = small_refine(a, sm, nullptr, gtimer());
+    }
     if (threadIdx.x == 0) {
       if (o.err) atomicOr(&B.ctrl->err, o.err);
       it.ss[B.words.b] = o.num_blocks;
@@ -405,6 +575,14 @@ int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "launch of the single-block kernel");
   return DFA_OK;
+}
+
+bool medium_block_plan(uint32_t n, uint32_t log2S, uint32_t *plan, size_t *smem) {
+  if (n < 1 || n > 65536u) return false;
+  const uint32_t log2T = log2S + 1;   // slots at a load of at most 1/4, within the DFA's table region
+  *plan = log2T | (1u << 10);
+  *smem = (size_t)((n + 7u) & ~7u) * 2;
+  return true;
 }
 
 bool small_block_plan(uint32_t n, uint32_t k, uint32_t *plan, size_t *smem) {

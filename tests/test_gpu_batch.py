@@ -149,13 +149,34 @@ def test_batch_4096_full_size(g):
         assert np.array_equal(b, alone.cpu().numpy().view(np.uint32)), i
 
 
+def test_batch_medium_dfas_planted(g):
+    """DFAs of 16,385 to 65,536 states with true merges (planted redundancy)
+    and with many letters, on the block-per-DFA path with the table in global
+    memory, against the oracle and Hopcroft's partition."""
+    dfas = [dfagen.planted_redundancy(dfagen.random_dfa(n, k, 0.5, 70 + n), c, 71 + k)[0]
+            for n, k, c in ((5000, 3, 7), (8000, 2, 8), (2000, 8, 30), (13_000, 5, 5))]
+    dfas.append(dfagen.random_dfa(60_000, 2, 0.0, 9))       # no accepting state: one block
+    dfas.append(dfagen.chain_dfa(20_000))                   # 19,999 rounds: the round tags wrap
+    assert all(16_384 < A.n <= 65_536 for A in dfas)
+    blocks, res = _batch(g, dfas, schedule=6)
+    for i, (A, b, r) in enumerate(zip(dfas, blocks, res)):
+        ref = oracle.moore(A.delta, A.accept)
+        assert np.array_equal(b, ref.block), i
+        assert (r.num_blocks, r.rounds_changed, r.rounds_executed) == \
+            (ref.num_blocks, ref.rounds_changed, ref.rounds_executed), i
+        if A.n < 30_000:
+            assert np.array_equal(b, oracle.hopcroft(A.delta, A.accept)), i
+
+
 @pytest.mark.parametrize("schedule", [0, 6])
 def test_batch_recipe_both_paths(g, schedule):
-    """512 DFAs of the batch recipe, sizes from 64 to 65,536 states: with
-    schedule 6 the DFAs that fit one block are refined one per block and the
-    rest by the cooperative kernel, in the same call; every partition and
-    round count equals the oracle's."""
+    """512 DFAs of the batch recipe (64 to 65,536 states) and two beyond 65,536:
+    with schedule 6 the DFAs that fit one block's shared memory, and those of
+    up to 65,536 states with the table in global memory, are refined one per
+    block, the two largest by the cooperative kernel, in the same call; every
+    partition and round count equals the oracle's."""
     dfas = dfagen.batch_dfas(512, 64, 65_536, 2, 8, 0.3, 41)
+    dfas += [dfagen.random_dfa(70_000, 3, 0.3, 42), dfagen.random_dfa(66_000, 8, 0.3, 43)]
     assert any(A.n > 16_384 for A in dfas) and any(A.n <= 16_384 for A in dfas)
     blocks, res = _batch(g, dfas, schedule=schedule)
     for i, (A, b, r) in enumerate(zip(dfas, blocks, res)):
@@ -166,18 +187,22 @@ def test_batch_recipe_both_paths(g, schedule):
 
 
 def test_batch_block_per_dfa_limits(g):
-    """Round limit and an invalid target on the block-per-DFA path."""
-    dfas = [dfagen.chain_dfa(50), dfagen.random_dfa(100, 2, 0.5, 3), dfagen.random_dfa(30_000, 3, 0.5, 4)]
+    """Round limit and an invalid target on the block-per-DFA path (both the
+    shared-memory and the global-table refinement)."""
+    dfas = [dfagen.chain_dfa(50), dfagen.random_dfa(100, 2, 0.5, 3), dfagen.random_dfa(30_000, 3, 0.5, 4),
+            dfagen.chain_dfa(40_000)]
     blocks, res = _batch(g, dfas, schedule=6, max_rounds=3, check=False)
     for A, b, r in zip(dfas, blocks, res):
         ref = oracle.moore(A.delta, A.accept, max_rounds=3)
         assert np.array_equal(b, oracle.canonical(ref.block))
         assert r.rounds_executed == ref.rounds_executed
     assert res[0].status == g.DFA_EMAXROUNDS
-    B = dfagen.random_dfa(50, 2, 0.5, 4)
-    B.delta[1][7] = 50
-    with pytest.raises(g.DfaError):
-        _batch(g, [dfagen.random_dfa(100, 2, 0.5, 3), B], schedule=6)
+    for nB in (50, 40_000):   # a DFA held in shared memory, and one with its table in global memory
+        B = dfagen.random_dfa(nB, 2, 0.5, 4)
+        B.delta[1][7] = nB
+        with pytest.raises(g.DfaError):
+            _batch(g, [dfagen.random_dfa(100, 2, 0.5, 3), B], schedule=6)
+    _batch(g, [dfagen.random_dfa(100, 2, 0.5, 3)], schedule=6)   # the context survives
 
 
 def test_batch_max_rounds(g):
