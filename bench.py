@@ -400,7 +400,8 @@ def extras(g):
 def schedule_name(s):
     """The batch kernel's schedule s: states per lane, states per tile, and whether
     the DFAs that fit one thread block are refined one per block."""
-    return f"{1 + (s & 1)} state(s) per lane, tile {256 >> ((s >> 1) % 3)}" + (", block per small DFA" if s >= 6 else "")
+    return f"{1 + (s & 1)} state(s) per lane, tile {256 >> ((s >> 1) % 3)}" + \
+        (", block per DFA of up to 65,536 states" if s >= 6 else "")
 
 
 def autotune_record():
@@ -563,7 +564,12 @@ def run_batch_case(args, local):
         el = time.perf_counter() - t
     tune = autotune_record() if args.schedule < 0 else None
     chosen = next(iter(tune.values()))["choice"] if tune else schedule_name(args.schedule)
-    launches = 2 if "block per small DFA" in chosen else 1   # the cooperative kernel, then the block-per-DFA one
+    # the cooperative kernel and/or the block-per-DFA kernel: with blocks, the cooperative
+    # launch runs only for DFAs beyond 65,536 states
+    if "block per DFA" in chosen:
+        launches = 1 + (1 if int(pn.max()) > 65_536 else 0)
+    else:
+        launches = 1
     print(json.dumps({"metric": "DFAs minimised/sec (batched)", "value": args.batch_dfas * args.steps / el,
                       "unit": "DFAs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": el * 1e3 / args.steps, "device_ms": statistics.median(dev) / 1e6,

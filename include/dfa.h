@@ -125,8 +125,8 @@ typedef struct dfa_opts {
   uint64_t timeout_ns;     /* 0 = library default (600 s); limit on the whole call's device work */
   int32_t schedule;        /* -1 = autotune / default; >= 0 selects a kernel schedule.  Batch
                               calls: 0..11, 1 + (s & 1) states per lane, 256 >> ((s >> 1) % 3)
-                              states per tile, and from 6 on every DFA that fits one thread
-                              block refined alone by one block (DFA_EINVAL beyond 11; -1 lets
+                              states per tile, and from 6 on every DFA of at most 65,536 states
+                              refined alone by one thread block (DFA_EINVAL beyond 11; -1 lets
                               the autotuner time all twelve once per batch shape, see
                               dfa_minimise_batch).
                               dfa_minimise: 1, 2 or 4 forces the cooperative kernel with that
@@ -186,9 +186,11 @@ size_t dfa_batch_workspace_size(const dfa_t *dfas, uint32_t count, const dfa_opt
  * $DFA_AUTOTUNE_CACHE (default ~/.cache/dfa_gb300_autotune.json), one line per
  * shape: "batch|<GPU>|states2^a|dfas2^b|kmaxc": [choice, ns_0, ..., ns_11].
  * The launch is a CUDA graph (control-block reset + the cooperative kernel,
- * then for schedules 6..11 the kernel that refines the DFAs fitting one block
- * one per block), instantiated once per host thread and graph shape and
- * updated in place by later calls (dfa_batch_graph_stats counts both). */
+ * then for schedules 6..11 the kernel that refines the DFAs of at most 65,536
+ * states one per block, the cooperative kernel then refining only the larger
+ * ones and left out when there are none), instantiated once per host thread
+ * and graph shape and updated in place by later calls (dfa_batch_graph_stats
+ * counts both). */
 int dfa_minimise_batch(const dfa_t *dfas, uint32_t count, const dfa_opts *opts, uint32_t *block_out,
                        dfa_result *res, void *workspace, size_t ws_bytes, void *stream);
 
