@@ -1,4 +1,7 @@
-// Signature refinement of a small DFA in one thread block.
+// Signature refinement of a DFA in one thread block: the single-DFA kernel for
+// up to kSmallMaxStates states (everything in shared memory), and the batches'
+// block-per-DFA kernel, which also refines DFAs of up to 65,536 states with
+// only their labels in shared memory (medium_refine, further below).
 //
 // Algorithm 4 (Section 3.3) on a state space that fits in shared memory
 // (n <= kSmallMaxStates): the labels of two consecutive rounds (16-bit), the
