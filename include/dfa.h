@@ -249,7 +249,10 @@ size_t dfa_equivalent_workspace_size(const dfa_t *a, const dfa_t *b, const dfa_o
  * or 0.  res describes the union's refinement; with DFA_FLAG_EARLY_EXIT the
  * refinement stops at the first round that separates the start states, and
  * res->rounds_executed is then the length of a shortest word that A and B
- * disagree on. */
+ * disagree on.  A union of at most 16,384 states is refined by the same
+ * small kernels as dfa_minimise (one thread block or one cluster; the
+ * DFA_FLAG_ONE_BLOCK / DFA_FLAG_CLUSTER flags and an explicit schedule apply
+ * as there), with the same results. */
 int dfa_equivalent(const dfa_t *a, const dfa_t *b, const dfa_opts *opts, int *equivalent,
                    dfa_result *res, void *workspace, size_t ws_bytes, void *stream);
 

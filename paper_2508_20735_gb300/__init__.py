@@ -304,11 +304,11 @@ def minimise(delta, accept, algo="moore", max_rounds=0, timeout_ns=0, out=None, 
     return out, res
 
 
-def equivalent(A, B, early_exit=False, timeout_ns=0, workspace=None, stream=None, check=True, flags=0):
+def equivalent(A, B, early_exit=False, timeout_ns=0, workspace=None, stream=None, check=True, flags=0, schedule=-1):
     """L(A) = L(B)?  A and B are (delta, accept, start) triples.  Returns (bool, DfaResult)."""
     a, ka = make_dfa(A[0], A[1], A[2])
     b, kb = make_dfa(B[0], B[1], B[2])
-    o = make_opts("moore", 0, timeout_ns, flags=(DFA_FLAG_EARLY_EXIT if early_exit else 0) | int(flags))
+    o = make_opts("moore", 0, timeout_ns, schedule, flags=(DFA_FLAG_EARLY_EXIT if early_exit else 0) | int(flags))
     need = dfa_equivalent_workspace_size(a, b, o)
     if need == 0:
         raise DfaError(DFA_EINVAL, last_error() or "bad arguments")

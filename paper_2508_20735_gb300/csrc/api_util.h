@@ -56,8 +56,10 @@ int status_from_ctrl(const Ctrl &c);
 // dfa_minimise_async when small_fits; results in *ctrl.
 static constexpr uint32_t kSmallMaxStates = 16384;
 bool small_fits(uint32_t n, uint32_t k, const dfa_opts &o);
+// track (may be null): equivalence by union, the start pair whose separating
+// round goes to ctrl->sep_round (~0: never apart), with early exit on request.
 int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
-                  const dfa_opts &o, cudaStream_t st);
+                  const dfa_opts &o, cudaStream_t st, const PairTrack *track = nullptr);
 // Batches (batch.cu): a DFA refined alone by one thread block of small.cu's
 // kernel; plan = log2 T | wide table << 8 | staged δ << 9 (small_block_plan:
 // everything in shared memory), or log2 T | 1 << 10 (medium_block_plan: up to
@@ -92,7 +94,7 @@ cudaError_t enqueue_batch_small(const BatchSmallItem *items, uint32_t count, uin
 // one and the DFA fits; enqueue_small decides between the two.
 bool cluster_fits(uint32_t n, uint32_t k);
 int enqueue_cluster(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
-                    const dfa_opts &o, cudaStream_t st);
+                    const dfa_opts &o, cudaStream_t st, const PairTrack *track = nullptr);
 
 // naivePR / transPR (naive.cu)
 size_t naive_workspace_size(const dfa_t *d, const dfa_opts &o);

@@ -65,6 +65,9 @@ struct ClusterArgs {
   uint32_t max_rounds;     // 0 = none
   uint32_t stop_discrete;  // 1: stop after a round that leaves n blocks
   unsigned long long timeout_ns;
+  uint32_t track;          // equivalence by union: record the first round after which sa and sb are apart
+  uint32_t sa, sb;
+  uint32_t early_exit;     // with track: stop there (round 0: no round at all)
 };
 
 // Shared memory of one CTA (bytes), for the layout the kernel uses:
@@ -152,7 +155,12 @@ __global__ void __launch_bounds__(kClusterThreads, 1) moore_cluster_kernel(const
   uint32_t nt = 0;   // trace entries (CTA 0, thread 0)
   if (me == 0 && tid == 0) trace_put(Cc, nt, t0, kTraceStart);
   uint32_t B_prev = any_acc + any_rej, B_r = B_prev;
-  uint32_t r = 0, changed = 0, cur = 0, maxed = 0, w = 1;
+  uint32_t r = 0, changed = 0, cur = 0, maxed = 0, w = 1, sep = 0xFFFFFFFFu;
+  bool skip = false;
+  if (A.track && (A.accept[A.sa] != 0) != (A.accept[A.sb] != 0)) {   // the empty word separates them
+    sep = 0;
+    skip = A.early_exit != 0;   // the answer needs no round: the initial partition is reported
+  }
   // δ(q, a): the shared copy, or global memory (an invalid target reads as 0 and is reported)
   auto target = [&](uint32_t a, uint32_t q) -> uint32_t {
     if (A.staged == 1) return d16[(size_t)a * n + q];
@@ -168,7 +176,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) moore_cluster_kernel(const
   auto slot_ptr = [&](unsigned long long *tab, uint32_t g) -> unsigned long long * {
     return cl.map_shared_rank(tab, g >> log2S) + (g & (S - 1u));
   };
-  for (r = 1; !err; ++r) {
+  for (r = 1; !err && !skip; ++r) {
     const uint16_t *src = cur ? lab1 : lab0;
     uint16_t *dst = cur ? lab0 : lab1;
     const uint32_t K = (k + 1u) * w;
@@ -276,6 +284,13 @@ __global__ void __launch_bounds__(kClusterThreads, 1) moore_cluster_kernel(const
     if (err) break;
     const bool grew = B_r != B_prev;
     if (grew) ++changed;
+    if (A.track && sep == 0xFFFFFFFFu) {   // every CTA holds all new labels now: a uniform decision
+      const uint16_t *nl = cur ? lab1 : lab0;
+      if (nl[A.sa] != nl[A.sb]) {
+        sep = r;
+        if (A.early_exit) break;
+      }
+    }
     if (!grew) break;   // Algorithm 4's until-test: the round added no block
     if (A.stop_discrete && B_r == n) break;
     if (A.max_rounds != 0u && r >= A.max_rounds) {
@@ -284,6 +299,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) moore_cluster_kernel(const
     }
     B_prev = B_r;
   }
+  if (skip) r = 0;
+  if (me == 0 && tid == 0) Cc->sep_round = sep;
   if (err) {
     if (me == 0 && tid == 0) {
       Cc->err = err;
@@ -405,7 +422,7 @@ bool cluster_fits(uint32_t n, uint32_t k) {
 }
 
 int enqueue_cluster(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
-                    const dfa_opts &o, cudaStream_t st) {
+                    const dfa_opts &o, cudaStream_t st, const PairTrack *track) {
   const uint32_t l2 = cluster_log2_size();
   ClusterPlan p;
   if (l2 == 0 || !cluster_plan(n, k, l2, &p)) return fail(DFA_EINVAL, "the cluster kernel does not fit %u states", n);
@@ -423,6 +440,12 @@ int enqueue_cluster(const uint32_t *delta, const uint8_t *accept, uint32_t n, ui
   a.max_rounds = o.max_rounds;
   a.stop_discrete = (o.flags & DFA_FLAG_STOP_DISCRETE) ? 1u : 0u;
   a.timeout_ns = o.timeout_ns;
+  if (track) {
+    a.track = 1u;
+    a.sa = track->a;
+    a.sb = track->b;
+    a.early_exit = track->early_exit;
+  }
   cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ctrl)");
   cudaLaunchConfig_t cfg{};

@@ -107,10 +107,19 @@ int dfa_equivalent(const dfa_t *a, const dfa_t *b, const dfa_opts *opts, int *eq
   if (e != cudaSuccess) return cuda_fail(e, "read union status");
   PairTrack tr{a->start, a->n + b->start, (o.flags & DFA_FLAG_EARLY_EXIT) ? 1u : 0u};
   uint32_t *out = reinterpret_cast<uint32_t *>(ws + L.out);
-  const uint32_t vec_ok = pick_vec(n_u, k, du, au, o.schedule);
   Ctrl c{};
-  rc = run_moore(du, au, n_u, k, out, L, ws, o, st, &tr, &c, vec_ok);
-  if (rc != DFA_OK) return rc;
+  if (small_fits(n_u, k, o)) {   // a union of at most 16,384 states: one thread block or one cluster
+    Ctrl *cd = reinterpret_cast<Ctrl *>(ws + L.ctrl);
+    rc = enqueue_small(du, au, n_u, k, out, cd, o, st, &tr);
+    if (rc != DFA_OK) return rc;
+    e = cudaMemcpyAsync(&c, cd, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "refinement of the union");
+  } else {
+    const uint32_t vec_ok = pick_vec(n_u, k, du, au, o.schedule);
+    rc = run_moore(du, au, n_u, k, out, L, ws, o, st, &tr, &c, vec_ok);
+    if (rc != DFA_OK) return rc;
+  }
   if (err_host & ERR_BAD_DELTA) return fail(DFA_EINVAL, "a transition target is >= n");
   const int status = status_from_ctrl(c);
   if (res) {

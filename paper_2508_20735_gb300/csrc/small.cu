@@ -47,6 +47,9 @@ struct SmallArgs {
   uint32_t max_rounds;     // 0 = none
   uint32_t stop_discrete;  // 1: stop after a round that leaves n blocks
   unsigned long long timeout_ns;
+  uint32_t track;          // equivalence by union: record the first round after which sa and sb are apart
+  uint32_t sa, sb;
+  uint32_t early_exit;     // with track: stop there (round 0: no round at all)
 };
 
 __device__ __forceinline__ uint32_t small_mix(uint32_t h, uint32_t v) {
@@ -57,6 +60,7 @@ __device__ __forceinline__ uint32_t small_mix(uint32_t h, uint32_t v) {
 // What one refinement in a block produced.
 struct SmallOut {
   uint32_t err, rounds_executed, rounds_changed, num_blocks, maxed;
+  uint32_t sep_round;   // with A.track: first round that separated sa and sb (0: their acceptance), else ~0
 };
 
 // The refinement of one DFA by the calling block (every thread takes part),
@@ -90,7 +94,12 @@ __device__ __forceinline__ SmallOut small_refine(const SmallArgs &A, uint32_t *s
   const uint32_t classes = block_sum(((seen & 1u) ? 1u : 0u) | ((seen & 2u) ? 0x10000u : 0u), s_red);
   const uint32_t any_acc = (classes & 0xFFFFu) != 0u, any_rej = (classes >> 16) != 0u;
   uint32_t B_prev = any_acc + any_rej, B_r = B_prev;
-  uint32_t r = 0, changed = 0, cur = 0, maxed = 0, err = s_flag, w = 1;
+  uint32_t r = 0, changed = 0, cur = 0, maxed = 0, err = s_flag, w = 1, sep = 0xFFFFFFFFu;
+  bool skip = false;
+  if (A.track && (A.accept[A.sa] != 0) != (A.accept[A.sb] != 0)) {   // the empty word separates them
+    sep = 0;
+    skip = A.early_exit != 0;   // the answer needs no round: the initial partition is reported
+  }
   uint32_t nt = 0;   // trace entries (thread 0)
   if (tid == 0 && C) trace_put(C, nt, t0, kTraceStart);
   // δ(q, a): the shared copy, or global memory (an invalid target reads as 0 and is reported)
@@ -103,7 +112,7 @@ __device__ __forceinline__ SmallOut small_refine(const SmallArgs &A, uint32_t *s
     }
     return d;
   };
-  for (r = 1; !err; ++r) {
+  for (r = 1; !err && !skip; ++r) {
     const uint16_t *src = cur ? lab1 : lab0;
     uint16_t *dst = cur ? lab0 : lab1;
     const uint32_t K = (k + 1u) * w;
@@ -203,6 +212,13 @@ __device__ __forceinline__ SmallOut small_refine(const SmallArgs &A, uint32_t *s
     }
     const bool grew = B_r != B_prev;
     if (grew) ++changed;
+    if (A.track && sep == 0xFFFFFFFFu) {   // the new labels, read after the round's barriers: uniform
+      const uint16_t *nl = cur ? lab1 : lab0;
+      if (nl[A.sa] != nl[A.sb]) {
+        sep = r;
+        if (A.early_exit) break;
+      }
+    }
     if (!grew) break;   // Algorithm 4's until-test: the round added no block
     if (A.stop_discrete && B_r == n) break;
     if (A.max_rounds != 0u && r >= A.max_rounds) {
@@ -220,7 +236,8 @@ __device__ __forceinline__ SmallOut small_refine(const SmallArgs &A, uint32_t *s
     }
     B_prev = B_r;
   }
-  if (err) return SmallOut{err, r, changed, 0u, maxed};
+  if (skip) r = 0;
+  if (err) return SmallOut{err, r, changed, 0u, maxed, sep};
   // canonical numbering: blocks in order of their smallest state (every label
   // is below T: a slot, or a direct signature of at most log2 T bits)
   const uint16_t *fin = cur ? lab1 : lab0;
@@ -249,7 +266,7 @@ __device__ __forceinline__ SmallOut small_refine(const SmallArgs &A, uint32_t *s
     blocks = total;
   }
   if (tid == 0 && C) trace_put(C, nt, t0, kTraceEnd);
-  return SmallOut{0u, r, changed, blocks, maxed};
+  return SmallOut{0u, r, changed, blocks, maxed, sep};
 }
 
 // A DFA of at most 65,536 states refined by one block with its labels in
@@ -373,7 +390,7 @@ __device__ __forceinline__ SmallOut medium_refine(const MediumArgs &A, uint16_t 
     }
     B_prev = B_r;
   }
-  if (err) return SmallOut{err, r, changed, 0u, maxed};
+  if (err) return SmallOut{err, r, changed, 0u, maxed, 0xFFFFFFFFu};
   __syncthreads();   // the last labels are in shared memory
   // canonical numbering: blocks in order of their smallest state (labels are
   // representatives, so below n)
@@ -400,7 +417,7 @@ __device__ __forceinline__ SmallOut medium_refine(const MediumArgs &A, uint16_t 
     for (uint32_t q = tid; q < n; q += bd) A.out[q] = A.minrep[L[q]] & 0x7FFFFFFFu;
     blocks = total;
   }
-  return SmallOut{0u, r, changed, blocks, maxed};
+  return SmallOut{0u, r, changed, blocks, maxed, 0xFFFFFFFFu};
 }
 
 __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __grid_constant__ SmallArgs A) {
@@ -418,6 +435,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) moore_small_kernel(const __g
       C->num_blocks = o.num_blocks;
       C->maxed = o.maxed;
     }
+    C->sep_round = o.sep_round;
     C->t_end = gtimer();
   }
 }
@@ -552,9 +570,9 @@ static SmallKernel pick_small(uint32_t n, uint32_t k, const dfa_opts &o) {
 bool small_fits(uint32_t n, uint32_t k, const dfa_opts &o) { return pick_small(n, k, o) != SK_NONE; }
 
 int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint32_t k, uint32_t *out, Ctrl *ctrl,
-                  const dfa_opts &o, cudaStream_t st) {
+                  const dfa_opts &o, cudaStream_t st, const PairTrack *track) {
   const SmallKernel which = pick_small(n, k, o);
-  if (which == SK_CLUSTER) return enqueue_cluster(delta, accept, n, k, out, ctrl, o, st);
+  if (which == SK_CLUSTER) return enqueue_cluster(delta, accept, n, k, out, ctrl, o, st, track);
   const SmallPlan p = small_plan(n, k);
   if (p.smem == 0) return fail(DFA_EINVAL, "the single-block kernel does not fit %u states", n);
   SmallArgs a{};
@@ -570,6 +588,12 @@ int enqueue_small(const uint32_t *delta, const uint8_t *accept, uint32_t n, uint
   a.max_rounds = o.max_rounds;
   a.stop_discrete = (o.flags & DFA_FLAG_STOP_DISCRETE) ? 1u : 0u;
   a.timeout_ns = o.timeout_ns;
+  if (track) {
+    a.track = 1u;
+    a.sa = track->a;
+    a.sb = track->b;
+    a.early_exit = track->early_exit;
+  }
   cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ctrl)");
   e = cudaFuncSetAttribute(moore_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);

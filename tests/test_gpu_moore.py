@@ -445,3 +445,31 @@ def test_small_kernels_unaligned_inputs(g, n, k):
         block, res = g.minimise(d.view(k, n), a, **kw)
         assert np.array_equal(block.cpu().numpy().view(np.uint32), ref.block)
         assert (res.rounds_changed, res.rounds_executed) == (ref.rounds_changed, ref.rounds_executed)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_small_union_equivalence_all_kernels(g, seed):
+    """Equivalence by union for unions of at most 16,384 states: the single
+    block, the cluster and the cooperative kernel give the same verdict and
+    the same refinement (rounds, blocks), with and without early exit, and
+    the verdict equals the oracle's; start states apart by acceptance alone
+    take round 0."""
+    pairs = [dfagen.equivalence_pair(seed * 10 + i, 17, n_lo=200, n_hi=7000) for i in range(3)]
+    A = dfagen.random_dfa(900 + seed, 2, 0.5, seed)
+    B_acc = A.accept.copy()
+    B_acc[A.start] ^= 1
+    pairs.append((A, dfagen.DFA(A.delta.copy(), B_acc, A.start), False))
+    for A, B, expect in pairs:
+        if A.n + B.n > 16_384:
+            continue
+        args = ((A.delta, A.accept, A.start), (B.delta, B.accept, B.start))
+        ref = oracle.equivalent(A.delta, A.accept, A.start, B.delta, B.accept, B.start)
+        assert ref.equivalent == bool(expect)
+        for early in (False, True):
+            base_eq, base = g.equivalent(*args, early_exit=early, schedule=1)   # cooperative kernel
+            assert base_eq == bool(expect)
+            for flags in (0, g.DFA_FLAG_ONE_BLOCK, g.DFA_FLAG_CLUSTER):
+                eq, res = g.equivalent(*args, early_exit=early, flags=flags)
+                assert eq == base_eq, (flags, early)
+                assert (res.num_blocks, res.rounds_changed, res.rounds_executed) == \
+                    (base.num_blocks, base.rounds_changed, base.rounds_executed), (flags, early)
