@@ -255,7 +255,7 @@ def dfa_minimise_batch(dfas, opts: DfaOpts | None, block_out_ptr: int, workspace
     res = (DfaResult * len(arr))()
     st = lib().dfa_minimise_batch(arr, len(arr), ctypes.byref(opts) if opts else None, block_out_ptr, res,
                                   workspace_ptr, ws_bytes, stream)
-    return st, list(res)
+    return st, res   # the ctypes array: indexable and iterable, elements built on access
 
 
 def dfa_batch_packed_workspace_size(count: int, n_ptr: int, k_ptr: int, delta_ptr, accept_ptr: int,
@@ -271,7 +271,7 @@ def dfa_minimise_batch_packed(count: int, n_ptr: int, k_ptr: int, delta_ptr, acc
     st = lib().dfa_minimise_batch_packed(count, n_ptr, k_ptr, delta_ptr, accept_ptr,
                                          ctypes.byref(opts) if opts else None, block_out_ptr, res, workspace_ptr,
                                          ws_bytes, stream)
-    return st, list(res)
+    return st, res   # the ctypes array: indexable and iterable, elements built on access
 
 
 # ----------------------------------------------------------------- conveniences

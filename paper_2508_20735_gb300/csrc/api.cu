@@ -41,10 +41,8 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-uint32_t ceil_log2(uint64_t x) {
-  uint32_t b = 0;
-  while ((1ull << b) < x) ++b;
-  return b;
+uint32_t ceil_log2(uint64_t x) {   // smallest b with 2^b >= x
+  return x <= 1 ? 0u : 64u - (uint32_t)__builtin_clzll(x - 1);
 }
 
 dfa_opts default_opts(const dfa_opts *o) {

@@ -820,7 +820,9 @@ struct BatchLayout {
   uint64_t total_states, total_slots;
   uint32_t ntiles, max_stages, ebits;
   size_t stage_bytes;
+  uint32_t ntiles_by[3];   // tiles of 256, 128 and 64 states (summed by the same pass)
 };
+static void batch_place(BatchLayout &L, uint32_t count, uint32_t tile, uint32_t ntiles);
 
 // Warps of the batch kernel's cooperative grid (the larger of the two
 // schedules' grids); without a visible device, the largest grid the launcher
@@ -885,6 +887,7 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchIn
     }
     if (tile_off_out) tile_off_out->push_back(ntiles);
     ntiles += (d.n + tile - 1) / tile;
+    for (int t = 0; t < 3; ++t) L.ntiles_by[t] += (d.n + (256u >> t) - 1) >> (8 - t);
     // host-resident arrays are staged into the workspace
     const bool hd = in.host[2 * i], ha = in.host[2 * i + 1];
     const size_t db = (size_t)d.k * d.n * 4, ab = d.n;
@@ -907,24 +910,33 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchIn
     if (segs_out) segs_out->push_back(s);
   }
   if (tile_off_out) tile_off_out->push_back(ntiles);
+  (void)multi;
+  L.total_states = st;
+  L.total_slots = sl;
+  L.max_stages = max_stages;
+  L.ebits = ebits;
+  L.stage_bytes = stage_bytes;
+  batch_place(L, count, tile, ntiles);
+  return L;
+}
+
+// The workspace offsets of a batch whose totals the pass above has summed, for
+// `tile` states per tile and `ntiles` tiles.
+static void batch_place(BatchLayout &L, uint32_t count, uint32_t tile, uint32_t ntiles) {
+  const uint64_t st = L.total_states, sl = L.total_slots;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t at = off;
     off += (bytes + 255) / 256 * 256;
     return at;
   };
-  L.total_states = st;
-  L.total_slots = sl;
   L.ntiles = ntiles;
-  L.max_stages = max_stages;
-  L.ebits = ebits;
   L.ctrl = take(sizeof(Ctrl));
   L.segs = take(sizeof(SegInfo) * count);
   L.tile_off = take(((size_t)count + 1) * 4);
   L.tiles = take((size_t)ntiles * sizeof(Tile));
   L.lab0 = take(st * 4);
   L.lab1 = take(st * 4);
-  (void)multi;
   L.tmp = take(st * 4);   // multi-stage slots; filter buckets and slots
   L.tmp2 = take(st * 4);
   L.mbits = std::min<uint32_t>(31, std::max<uint32_t>(12, ceil_log2(st) + 2));
@@ -949,10 +961,8 @@ static BatchLayout batch_layout(const dfa_t *dfas, uint32_t count, const BatchIn
   L.ss = take((size_t)count * SS_WORDS * 4);
   L.items = take((size_t)count * sizeof(BatchSmallItem));
   L.small_next = take(4);
-  L.stage_bytes = stage_bytes;
-  L.stage = take(stage_bytes);
+  L.stage = take(L.stage_bytes);
   L.total = off;
-  return L;
 }
 
 static const void *batch_kernel_for(uint32_t vec) {
@@ -961,8 +971,17 @@ static const void *batch_kernel_for(uint32_t vec) {
 
 static size_t batch_max_warps() {
   const size_t fallback = kMaxGridB * (kBatchThreads / 32);
+  static std::atomic<size_t> known[64];   // per device, 0 = not looked up yet
   int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fallback;
+  }
+  if (dev >= 0 && dev < 64) {
+    const size_t k = known[dev].load(std::memory_order_relaxed);
+    if (k) return k;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     return fallback;
   }
@@ -975,6 +994,7 @@ static size_t batch_max_warps() {
     }
     best = std::max(best, (size_t)sms * (size_t)(per_sm < 1 ? 1 : per_sm) * (kBatchThreads / 32));
   }
+  if (dev >= 0 && dev < 64) known[dev].store(best, std::memory_order_relaxed);
   return best;
 }
 
@@ -1176,10 +1196,13 @@ static size_t batch_workspace_impl(const dfa_t *dfas, uint32_t count, const Batc
   uint64_t total;
   uint32_t kmax;
   if (check_batch(dfas, count, &total, &kmax) != DFA_OK) return 0;
+  // the workspace serves every schedule (they differ by tile): one pass over
+  // the DFAs, then the placement for each tile size
+  BatchLayout L = batch_layout(dfas, count, in, 256u, nullptr, nullptr, nullptr);
+  if (L.total_slots > 0xFFFFFFFFull) return 0;
   size_t most = 0;
-  for (uint32_t tile : {256u, 128u, 64u}) {   // the workspace serves every schedule (they differ by tile)
-    const BatchLayout L = batch_layout(dfas, count, in, tile, nullptr, nullptr, nullptr);
-    if (L.total_slots > 0xFFFFFFFFull) return 0;
+  for (int t = 0; t < 3; ++t) {
+    batch_place(L, count, 256u >> t, L.ntiles_by[t]);
     most = std::max(most, L.total);
   }
   return most;
