@@ -110,10 +110,10 @@ typedef enum dfa_algo {
                                       dfa_minimise_async and dfa_equivalent. */
 #define DFA_FLAG_GATHER 0x10u    /* signature refinement: never use the bucketed gather, even with
                                       DFA_FLAG_BUCKETED set; same results */
-#define DFA_FLAG_ONE_BLOCK 0x20u /* signature refinement of a DFA of at most 16,384 states: run
-                                      it in one thread block where it fits (else the cooperative
-                                      kernel); same results.  Honoured by dfa_minimise and
-                                      dfa_minimise_async. */
+#define DFA_FLAG_ONE_BLOCK 0x20u /* signature refinement of a DFA (or union) of at most 16,384
+                                      states: run it in one thread block where it fits (else the
+                                      cooperative kernel); same results.  Honoured by dfa_minimise,
+                                      dfa_minimise_async and dfa_equivalent. */
 #define DFA_FLAG_CLUSTER 0x40u   /* the same on one thread-block cluster where the GPU can place it
                                       (else the cooperative kernel); without either flag the call
                                       picks the cluster from 6,144 states on, or where one block
