@@ -19,7 +19,7 @@
 
 namespace dfa {
 
-static constexpr int kThreads = 512;
+static constexpr int kThreads = 1024;
 static constexpr int kBucketThreads = 512;
 
 // Vector loads/stores of VEC consecutive 32-bit values (VEC*4-byte aligned).
@@ -1172,7 +1172,7 @@ enum : uint32_t { MODE_DIRECT = 0, MODE_TABLE = 1, MODE_FILTER = 2 };
 // memory of BucketPlan::smem); rounds whose exact key needs several stages
 // keep the direct label reads.
 template <int VEC, bool BUCKET>
-__global__ void __launch_bounds__(BUCKET ? kBucketThreads : kThreads, BUCKET ? 1 : 2)
+__global__ void __launch_bounds__(BUCKET ? kBucketThreads : kThreads, 1)
     moore_kernel(const __grid_constant__ MooreArgs A) {
   __shared__ uint32_t s_red[32];
   __shared__ CtaCache cache;
