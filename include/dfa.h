@@ -188,8 +188,8 @@ size_t dfa_batch_workspace_size(const dfa_t *dfas, uint32_t count, const dfa_opt
  * The launch is a CUDA graph (control-block reset + the cooperative kernel,
  * then for schedules 6..11 the kernel that refines the DFAs of at most 65,536
  * states one per block, the cooperative kernel then refining only the larger
- * ones and left out when there are none), instantiated once per host thread
- * and graph shape and updated in place by later calls (dfa_batch_graph_stats
+ * ones and left out when there are none), instantiated once per host thread,
+ * device and graph shape and updated in place by later calls (dfa_batch_graph_stats
  * counts both). */
 int dfa_minimise_batch(const dfa_t *dfas, uint32_t count, const dfa_opts *opts, uint32_t *block_out,
                        dfa_result *res, void *workspace, size_t ws_bytes, void *stream);

@@ -1017,7 +1017,8 @@ struct GraphCache {
     if (cap) cudaStreamDestroy(cap);
   }
 };
-static thread_local GraphCache g_graphs;
+static constexpr int kGraphDevices = 64;
+static thread_local GraphCache g_graphs[kGraphDevices];   // per device: a capture stream belongs to one device
 static std::atomic<uint64_t> g_graph_instantiations{0}, g_graph_updates{0};
 
 // Launches the batch kernel as a CUDA graph: the control-block reset and the
@@ -1025,7 +1026,7 @@ static std::atomic<uint64_t> g_graph_instantiations{0}, g_graph_updates{0};
 // with `sl`, the reset of the DFA counter and the block-per-DFA kernel) are
 // captured on a library-owned stream (capture is not
 // allowed on the legacy default stream) and the graph runs on `st`.  The
-// instantiated graph is kept per host thread and per kernel variant: a later
+// instantiated graph is kept per host thread, per device and per graph shape: a later
 // call captures its own nodes (new pointers, new grid) and moves them into the
 // kept executable with cudaGraphExecUpdate, which costs a fraction of a new
 // instantiation; only when the update is refused is the graph instantiated
@@ -1033,8 +1034,11 @@ static std::atomic<uint64_t> g_graph_instantiations{0}, g_graph_updates{0};
 // executable run in order, so a call never changes a launch still in flight.
 static cudaError_t launch_batch_graph(const BatchArgs &a, int grid, bool coop, const SmallLaunch *sl,
                                       cudaStream_t st) {
-  GraphCache &G = g_graphs;
-  cudaError_t e;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kGraphDevices) return cudaErrorInvalidDevice;
+  GraphCache &G = g_graphs[dev];
   if (!G.cap && (e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
   cudaGraph_t graph = nullptr;
   e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
