@@ -206,6 +206,7 @@ MooreLayout moore_layout(uint64_t n, uint32_t k, bool stage_delta, bool stage_ac
   L.lab1 = take(n * 4);
   L.tmp = take(n * 4);
   const size_t warps = moore_max_warps();
+  L.warps = warps;
   L.dups = take((n + (warps + 2) * 32) * 4);   // n plus one partial chunk per warp
   L.dups2 = take((n + (warps + 2) * 32) * 4);
   L.wcnt = take(warps * 4);
@@ -321,6 +322,9 @@ int enqueue_moore(const uint32_t *delta_dev, const uint8_t *accept_dev, uint32_t
   e = moore_grid(a.vec, &li, a.bucket ? a.B_smem : 0);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   if ((size_t)li.grid > kMaxGrid) return fail(DFA_ECUDA, "grid of %d blocks exceeds %zu", li.grid, kMaxGrid);
+  if ((size_t)li.grid * (li.block / 32) > L.warps)   // the per-warp lists would overrun
+    return fail(DFA_ECUDA, "launch of %zu warps exceeds the %zu the workspace layout holds (internal error)",
+                (size_t)li.grid * (li.block / 32), L.warps);
   e = launch_moore(a, st, &li);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the refinement kernel");
   return DFA_OK;

@@ -16,6 +16,7 @@ struct MooreLayout {
   uint32_t log2S, mbits, wid, ebits;
   size_t ctrl, table, lab0, lab1, tmp, minrep, flag, partials, bm0, bm1, seen1, seen2, seen3, seen4, tmp2, rep, dups, dups2, wcnt, delta, accept, out,
       total;
+  size_t warps;            // warps of the largest launch the per-warp lists (dups, dups2, wcnt) hold
   bool bucket;             // the bucketed gather runs (plan below); its buffers follow
   BucketPlan plan;
   size_t et, es, val, seg, used, phash, pq, pcnt, list;
